@@ -1,0 +1,145 @@
+"""Pins of the oracle's line search and NGMRES family (Sec. 2.3, Algorithms 1-3).
+
+Linear-case equivalences (Sec. 2.3.2 and Sec. 3.2) pin the window bookkeeping, the least-squares
+set-up and the mixing switch exactly: with g(x) = A x - b (A SPD) and the Richardson map
+q(x) = x - rho g(x), NGMRES(inf) reproduces GMRES, and the alternating schemes reproduce restarted
+GMRES(w+1) at the cycle boundaries.
+"""
+import numpy as np
+import pytest
+
+from oracle import solver as so
+from oracle.problem import Problem
+from synth.inputs import workload
+
+
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    A = A @ A.T + n * np.eye(n)
+    b = rng.standard_normal(n)
+    return A, b, so.LinearProblem(A, b, rho=1.0 / np.linalg.norm(A, 2))
+
+
+def _iterates(L, n, **kw):
+    hist = []
+    so.ga_ngmres(L.evaluate, L.qmap, np.zeros(n), rel_tol=0.0, history=hist, **kw)
+    return [np.zeros(n)] + [h["v"] for h in hist]
+
+
+def test_lsq_matches_normal_equations_and_orthogonality():
+    rng = np.random.default_rng(0)
+    gq = rng.standard_normal(40)
+    gwin = [rng.standard_normal(40) for _ in range(4)]
+    beta = so.ngmres_lsq(gq, gwin)
+    D = np.stack([gq - gi for gi in gwin], axis=1)
+    ref = np.linalg.solve(D.T @ D, -D.T @ gq)
+    np.testing.assert_allclose(beta, ref, rtol=1e-12)
+    res = gq + D @ beta
+    assert np.abs(D.T @ res).max() < 1e-12
+
+
+def test_ngmres_infinite_window_equals_gmres():
+    n = 10
+    A, b, L = _spd(n, 1)
+    vs = _iterates(L, n, window=1000, sigma=1, tau=0, n_iter=8)
+    for k in range(1, 9):
+        np.testing.assert_allclose(vs[k], so.gmres_iterate(A, b, np.zeros(n), k), atol=1e-12)
+
+
+@pytest.mark.parametrize("sigma", [1, 2, 5])
+def test_tau_zero_is_ngmres_for_any_sigma(sigma):
+    n = 9
+    A, b, L = _spd(n, 2)
+    ref = _iterates(L, n, window=3, sigma=1, tau=0, n_iter=10)
+    got = _iterates(L, n, window=3, sigma=sigma, tau=0, n_iter=10)
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_fp_first_alternation_equals_restarted_gmres(w):
+    # aNGMRES(w)[sigma]-FP[w+1-sigma] (variant 2): the first cycle ends on GMRES(w+1) for every
+    # sigma; with sigma = 1 every cycle boundary (w+1) j is a restarted GMRES(w+1) iterate.
+    n = 12
+    A, b, L = _spd(n, 3)
+    steps = 3 * (w + 1)
+    rg = so.restarted_gmres_iterates(A, b, np.zeros(n), w + 1, steps)
+    for sigma in range(1, w + 2):
+        vs = _iterates(L, n, window=w, sigma=sigma, tau=w + 1 - sigma, n_iter=steps, variant=2)
+        np.testing.assert_allclose(vs[w + 1], rg[w + 1], atol=1e-12)
+    vs = _iterates(L, n, window=w, sigma=1, tau=w, n_iter=steps, variant=2)
+    for j in (1, 2, 3):
+        np.testing.assert_allclose(vs[(w + 1) * j], rg[(w + 1) * j], atol=1e-12)
+
+
+@pytest.mark.parametrize("w", [1, 2, 3])
+def test_ga_ngmres_sigma_one_is_restarted_gmres_shifted_by_one(w):
+    # GA-NGMRES(w; 1, w) (variant 1): after the first NGMRES step, iterate (w+1) j + 1 is the
+    # restarted GMRES(w+1) iterate (w+1) j started from v^(1).
+    n = 12
+    A, b, L = _spd(n, 4)
+    steps = 3 * (w + 1) + 1
+    vs = _iterates(L, n, window=w, sigma=1, tau=w, n_iter=steps)
+    rg = so.restarted_gmres_iterates(A, b, vs[1], w + 1, 3 * (w + 1))
+    for j in (1, 2, 3):
+        np.testing.assert_allclose(vs[(w + 1) * j + 1], rg[(w + 1) * j], atol=1e-12)
+
+
+def test_anderson_infinite_window_is_q_of_gmres():
+    # Linear case (Sec. 2.3.2): AA(inf) iterates are q applied to GMRES iterates, v^(k+1) = q(x_k).
+    n = 10
+    A, b, L = _spd(n, 5)
+    hist = []
+    so.ga_aa(L.evaluate, L.qmap, np.zeros(n), window=1000, sigma=1, tau=0, n_iter=7,
+             rel_tol=0.0, history=hist)
+    for k, h in enumerate(hist):
+        xk = so.gmres_iterate(A, b, np.zeros(n), k)
+        np.testing.assert_allclose(h["v"], L.qmap(xk, L.evaluate(xk)[0], None)[0], atol=1e-11)
+
+
+class _Quadratic:
+    """obj(v) = 1/2 ||v||^2, g = v, s = -g: closed-form Armijo decisions."""
+
+    def __init__(self):
+        self.calls = 0
+
+    def precond(self, g):
+        return -g
+
+    def inner(self, a, b):
+        return float(np.sum(a * b))
+
+    def objective(self, v):
+        self.calls += 1
+        return 0.5 * float(np.sum(v * v))
+
+
+def test_armijo_memory_closed_form():
+    p = _Quadratic()
+    q = so.ArmijoQ(p)
+    v = np.array([1.0, -2.0])
+    # rho = 1: obj(0) = 0 < obj(v) - c ||v||^2 -> accepted on the first trial -> memory 2
+    vq, oq = q(v, v, p.objective(v))
+    assert np.array_equal(vq, np.zeros(2)) and q.rho_mem == 2.0 and q.last_rho == 1.0
+    # rho = 2: obj(-v) = obj(v) is not a strict decrease -> halve to 1 -> accepted -> memory 1
+    vq, oq = q(v, v, p.objective(v))
+    assert q.last_rho == 1.0 and q.rho_mem == 1.0
+    # a direction that never decreases makes the search fail after max_backtracks halvings
+    bad = so.ArmijoQ(_Quadratic(), max_backtracks=5)
+    bad.p.precond = lambda g: g
+    with pytest.raises(so.LineSearchError):
+        bad(v, v, 0.5 * float(v @ v))
+    assert bad.trials == 6
+
+
+def test_ga_ngmres_beats_rpgd_on_small_transport_problem():
+    # Qualitative claim of Sec. 3.3: GA-NGMRES needs far fewer iterations than RPGD.
+    w = workload("adv2d64")
+    args = (w["m0"], w["m1"], w["nt"], w["model"], w["reg_order"], w["alpha"])
+    _, info_ng = so.solve_problem(Problem(*args), window=5, sigma=4, tau=2, n_iter=60, rel_tol=1e-2)
+    _, info_gd = so.solve_problem(Problem(*args), window=5, sigma=4, tau=2, n_iter=60, rel_tol=1e-2,
+                                  method="rpgd")
+    assert info_ng["converged"]
+    assert info_ng["iters"] < info_gd["iters"]
+    assert info_ng["rel_grad"] <= 1e-2
