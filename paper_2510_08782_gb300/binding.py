@@ -1,0 +1,392 @@
+"""ctypes binding of libga_gb300.so: the C ABI of include/ga.h and include/ga_ops.h.
+
+Argument marshalling only. Arrays may be torch tensors (CUDA tensors are passed as device
+pointers, CPU tensors as host pointers) or NumPy arrays (host pointers); they must be C-contiguous
+and of the context's element type (float64 for GA_PREC_FP64, float32 for GA_PREC_MIXED). Every
+compute call runs in the CUDA library; there is no Python or CPU fallback, and a missing library
+raises GaError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+GA_MODEL_ADVECTION, GA_MODEL_CONTINUITY, GA_MODEL_INCOMPRESSIBLE = 0, 1, 2
+GA_PREC_FP64, GA_PREC_MIXED = 0, 1
+GA_MEM_HOST, GA_MEM_DEVICE = 0, 1
+GA_METHOD_GA_NGMRES, GA_METHOD_RPGD = 0, 1
+STATUS = {0: "GA_OK", 1: "GA_ERR_ARG", 2: "GA_ERR_CUDA", 3: "GA_ERR_NOMEM", 4: "GA_ERR_NAN",
+          5: "GA_ERR_LINESEARCH", 6: "GA_ERR_NOT_CONVERGED", 7: "GA_ERR_TIMEOUT"}
+MODELS = {"advection": GA_MODEL_ADVECTION, "continuity": GA_MODEL_CONTINUITY,
+          "incompressible": GA_MODEL_INCOMPRESSIBLE}
+
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("dim", _c_int), ("n", _c_int * 3), ("nt", _c_int), ("model", _c_int),
+                ("reg_order", _c_int), ("alpha", _c_double), ("prec", _c_int), ("ckpt_every", _c_int)]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("window", _c_int), ("sigma", _c_int), ("tau", _c_int), ("max_iter", _c_int),
+                ("rel_tol", _c_double), ("armijo_c", _c_double), ("max_backtracks", _c_int),
+                ("variant", _c_int), ("method", _c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", _c_int), ("grad_evals", _c_int), ("obj_evals", _c_int), ("pde_solves", _c_int),
+                ("ls_trials", _c_int), ("last_branch", _c_int), ("converged", _c_int),
+                ("obj", _c_double), ("mismatch", _c_double), ("rel_grad_inf", _c_double),
+                ("grad_inf0", _c_double), ("rho_mem", _c_double), ("last_rho", _c_double),
+                ("t_grad_ms", _c_double), ("t_obj_ms", _c_double), ("t_total_ms", _c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class GaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libga_gb300.so")
+
+
+_LIB = None
+
+_SIGS = {
+    "ga_setup": ([ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOpts), _vp, _vp, _c_int, _vp,
+                  ctypes.POINTER(_vp)], _c_int),
+    "ga_objective": ([_vp, _vp, _c_int, ctypes.POINTER(_c_double)], _c_int),
+    "ga_gradient": ([_vp, _vp, _vp, _c_int, ctypes.POINTER(_c_double)], _c_int),
+    "ga_precond": ([_vp, _vp, _vp, _c_int], _c_int),
+    "ga_step": ([_vp, _vp, _c_int, ctypes.POINTER(Stats)], _c_int),
+    "ga_solve": ([_vp, _vp, _c_int, ctypes.POINTER(Stats)], _c_int),
+    "ga_reset": ([_vp], _c_int),
+    "ga_solve_batch": ([_c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_int, ctypes.POINTER(Stats)], _c_int),
+    "ga_get_stats": ([_vp, ctypes.POINTER(Stats)], _c_int),
+    "ga_destroy": ([_vp], None),
+    "ga_status_str": ([_c_int], ctypes.c_char_p),
+    "ga_last_error": ([_vp], ctypes.c_char_p),
+    "ga_op_departure": ([_vp, _vp, _vp, _vp], _c_int),
+    "ga_op_forward": ([_vp, _vp, _vp], _c_int),
+    "ga_op_adjoint": ([_vp, _vp, _vp, _vp], _c_int),
+    "ga_op_body_force": ([_vp, _vp, _vp, _vp], _c_int),
+    "ga_op_deriv": ([_vp, _vp, _c_int, _vp], _c_int),
+    "ga_op_div": ([_vp, _vp, _vp], _c_int),
+    "ga_op_fft_r2c": ([_vp, _vp, _vp], _c_int),
+    "ga_op_fft_c2r": ([_vp, _vp, _vp], _c_int),
+    "ga_op_apply_L": ([_vp, _vp, _vp], _c_int),
+    "ga_op_leray": ([_vp, _vp, _vp], _c_int),
+    "ga_op_dots": ([_vp, _vp, ctypes.POINTER(_vp), _c_int, ctypes.c_size_t, ctypes.POINTER(_c_double)], _c_int),
+    "ga_op_lsq": ([_vp, _c_int, _c_double, ctypes.POINTER(_c_double), ctypes.POINTER(_c_double),
+                   ctypes.POINTER(_c_double)], _c_int),
+    "ga_transport": ([_vp, _vp, _vp, _c_int], _c_int),
+    "ga_transport_vjp": ([_vp, _vp, _vp, _vp, _c_int], _c_int),
+    "ga_prof_start": ([_vp, _c_int], _c_int),
+    "ga_prof_stop": ([_vp, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)], _c_int),
+}
+
+
+def lib():
+    """The loaded CUDA library (raises GaError if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise GaError(2, f"CUDA library {path} is missing; build it with "
+                             "`python -m paper_2510_08782_gb300.build`")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _LIB = L
+    return _LIB
+
+
+def ga_status_str(status):
+    return lib().ga_status_str(int(status)).decode()
+
+
+def ga_last_error(ctx=None):
+    return lib().ga_last_error(ctx).decode()
+
+
+def _check(status, ctx=None, ok=(0,)):
+    if status not in ok:
+        raise GaError(status, ga_last_error(ctx))
+    return status
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(address, mem kind) of a C-contiguous array of element type dtype."""
+    if _is_torch(x):
+        import torch
+
+        want = torch.float64 if dtype == np.float64 else torch.float32
+        if x.dtype != want or not x.is_contiguous():
+            raise GaError(1, f"tensor must be contiguous {want}, got {x.dtype}")
+        return x.data_ptr(), (GA_MEM_DEVICE if x.is_cuda else GA_MEM_HOST)
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise GaError(1, f"array must be C-contiguous {np.dtype(dtype).name}, got {x.dtype}")
+        return x.ctypes.data, GA_MEM_HOST
+    raise GaError(1, f"unsupported array type {type(x)}")
+
+
+def _ptrs(dtype, *arrays):
+    out = [_ptr(a, dtype) for a in arrays]
+    kinds = {k for _, k in out}
+    if len(kinds) != 1:
+        raise GaError(1, "all arrays of one call must live in the same memory (host or device)")
+    return [p for p, _ in out], kinds.pop()
+
+
+def _current_stream():
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # torch absent: the legacy default stream
+        pass
+    return None
+
+
+# ---- raw C calls with the C names ------------------------------------------------------------------
+
+def ga_setup(desc, opts, m0, m1, stream=None):
+    """Create a context; returns (handle, element dtype)."""
+    dtype = np.float64 if desc.prec == GA_PREC_FP64 else np.float32
+    (p0, p1), mem = _ptrs(dtype, m0, m1)
+    h = _vp()
+    st = lib().ga_setup(ctypes.byref(desc), ctypes.byref(opts), p0, p1, mem,
+                        _vp(stream if stream is not None else _current_stream()), ctypes.byref(h))
+    _check(st, None)
+    return h.value
+
+
+def ga_destroy(ctx):
+    lib().ga_destroy(ctx)
+
+
+def ga_objective(ctx, dtype, v):
+    (pv,), mem = _ptrs(dtype, v)
+    out = _c_double()
+    _check(lib().ga_objective(ctx, pv, mem, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def ga_gradient(ctx, dtype, v, g):
+    (pv, pg), mem = _ptrs(dtype, v, g)
+    out = _c_double()
+    _check(lib().ga_gradient(ctx, pv, pg, mem, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def ga_precond(ctx, dtype, g, s):
+    (pg, ps), mem = _ptrs(dtype, g, s)
+    _check(lib().ga_precond(ctx, pg, ps, mem), ctx)
+
+
+def ga_step(ctx, dtype, v):
+    (pv,), mem = _ptrs(dtype, v)
+    stt = Stats()
+    st = lib().ga_step(ctx, pv, mem, ctypes.byref(stt))
+    _check(st, ctx)
+    return stt
+
+
+def ga_solve(ctx, dtype, v):
+    (pv,), mem = _ptrs(dtype, v)
+    stt = Stats()
+    st = lib().ga_solve(ctx, pv, mem, ctypes.byref(stt))
+    _check(st, ctx, ok=(0, 6))
+    return stt, st
+
+
+def ga_solve_batch(ctxs, dtype, vs):
+    ptrs, mem = _ptrs(dtype, *vs)
+    n = len(ctxs)
+    carr = (_vp * n)(*ctxs)
+    varr = (_vp * n)(*ptrs)
+    stats = (Stats * n)()
+    st = lib().ga_solve_batch(n, carr, varr, mem, stats)
+    _check(st, None, ok=(0, 6))
+    return list(stats), st
+
+
+def ga_reset(ctx):
+    _check(lib().ga_reset(ctx), ctx)
+
+
+def ga_transport(ctx, dtype, v, m1_out):
+    (pv, pm), mem = _ptrs(dtype, v, m1_out)
+    _check(lib().ga_transport(ctx, pv, pm, mem), ctx)
+
+
+def ga_transport_vjp(ctx, dtype, v, gamma, grad_v):
+    (pv, pgam, pg), mem = _ptrs(dtype, v, gamma, grad_v)
+    _check(lib().ga_transport_vjp(ctx, pv, pgam, pg, mem), ctx)
+
+
+def _dev(dtype, *arrays):
+    ptrs, mem = _ptrs(dtype, *arrays)
+    if mem != GA_MEM_DEVICE:
+        raise GaError(1, "operator-level calls take CUDA tensors")
+    return ptrs
+
+
+def ga_op_departure(ctx, dtype, v, xm, xp):
+    _check(lib().ga_op_departure(ctx, *_dev(dtype, v, xm, xp)), ctx)
+
+
+def ga_op_forward(ctx, dtype, v, states):
+    _check(lib().ga_op_forward(ctx, *_dev(dtype, v, states)), ctx)
+
+
+def ga_op_adjoint(ctx, dtype, v, lam1, lams):
+    _check(lib().ga_op_adjoint(ctx, *_dev(dtype, v, lam1, lams)), ctx)
+
+
+def ga_op_body_force(ctx, dtype, v, lam1, b):
+    _check(lib().ga_op_body_force(ctx, *_dev(dtype, v, lam1, b)), ctx)
+
+
+def ga_op_deriv(ctx, dtype, f, axis, df):
+    pf, pd = _dev(dtype, f, df)
+    _check(lib().ga_op_deriv(ctx, pf, int(axis), pd), ctx)
+
+
+def ga_op_div(ctx, dtype, v, mu):
+    _check(lib().ga_op_div(ctx, *_dev(dtype, v, mu)), ctx)
+
+
+def ga_op_fft_r2c(ctx, dtype, f, fhat):
+    _check(lib().ga_op_fft_r2c(ctx, *_dev(dtype, f, fhat)), ctx)
+
+
+def ga_op_fft_c2r(ctx, dtype, fhat, f):
+    _check(lib().ga_op_fft_c2r(ctx, *_dev(dtype, fhat, f)), ctx)
+
+
+def ga_op_apply_L(ctx, dtype, v, Lv):
+    _check(lib().ga_op_apply_L(ctx, *_dev(dtype, v, Lv)), ctx)
+
+
+def ga_op_leray(ctx, dtype, v, pv):
+    _check(lib().ga_op_leray(ctx, *_dev(dtype, v, pv)), ctx)
+
+
+def ga_op_dots(ctx, dtype, a, bs):
+    ptrs = _dev(dtype, a, *bs)
+    n = len(bs)
+    arr = (_vp * n)(*ptrs[1:])
+    out = (_c_double * n)()
+    _check(lib().ga_op_dots(ctx, ptrs[0], arr, n, int(np.prod(tuple(a.shape))), out), ctx)
+    return np.array(out[:])
+
+
+def ga_op_lsq(ctx, c, a, M):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    m = a.shape[0]
+    beta = np.zeros(m)
+    dp = ctypes.POINTER(_c_double)
+    _check(lib().ga_op_lsq(ctx, m, float(c), a.ctypes.data_as(dp), M.ctypes.data_as(dp),
+                           beta.ctypes.data_as(dp)), ctx)
+    return beta
+
+
+def ga_prof_start(ctx, kernel_class):
+    _check(lib().ga_prof_start(ctx, int(kernel_class)), ctx)
+
+
+def ga_prof_stop(ctx):
+    ms, n = _c_double(), ctypes.c_longlong()
+    _check(lib().ga_prof_stop(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+# ---- convenience object --------------------------------------------------------------------------
+
+class Problem:
+    """One problem context: m0, m1 on a periodic grid, model, regulariser and solver options.
+
+    m0, m1: arrays of shape n (2D or 3D). prec: 'fp64' or 'mixed'. Arrays passed to the methods
+    follow the binding rules above; vector fields have shape (dim, *n).
+    """
+
+    def __init__(self, m0, m1, nt, model="advection", reg_order=2, alpha=1e-3, prec="fp64",
+                 ckpt_every=0, window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2, armijo_c=1e-4,
+                 max_backtracks=20, variant=1, method="ga-ngmres", stream=None):
+        shape = tuple(int(s) for s in m0.shape)
+        self.shape = shape
+        self.dim = len(shape)
+        self.dtype = np.float64 if prec == "fp64" else np.float32
+        d = ProblemDesc()
+        d.dim = self.dim
+        for i, s in enumerate(shape):
+            d.n[i] = s
+        d.nt = int(nt)
+        d.model = MODELS[model]
+        d.reg_order = int(reg_order)
+        d.alpha = float(alpha)
+        d.prec = GA_PREC_FP64 if prec == "fp64" else GA_PREC_MIXED
+        d.ckpt_every = int(ckpt_every)
+        o = SolverOpts()
+        o.window, o.sigma, o.tau, o.max_iter = int(window), int(sigma), int(tau), int(max_iter)
+        o.rel_tol, o.armijo_c, o.max_backtracks = float(rel_tol), float(armijo_c), int(max_backtracks)
+        o.variant = int(variant)
+        o.method = GA_METHOD_RPGD if method == "rpgd" else GA_METHOD_GA_NGMRES
+        self.desc, self.opts = d, o
+        self.ctx = ga_setup(d, o, m0, m1, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ga_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def vshape(self):
+        return (self.dim,) + self.shape
+
+    def objective(self, v):
+        return ga_objective(self.ctx, self.dtype, v)
+
+    def gradient(self, v, g):
+        return ga_gradient(self.ctx, self.dtype, v, g)
+
+    def precond(self, g, s):
+        ga_precond(self.ctx, self.dtype, g, s)
+
+    def step(self, v):
+        return ga_step(self.ctx, self.dtype, v)
+
+    def solve(self, v):
+        return ga_solve(self.ctx, self.dtype, v)
+
+    def reset(self):
+        ga_reset(self.ctx)
+
+    def transport(self, v, m1_out):
+        ga_transport(self.ctx, self.dtype, v, m1_out)
+
+    def transport_vjp(self, v, gamma, grad_v):
+        ga_transport_vjp(self.ctx, self.dtype, v, gamma, grad_v)

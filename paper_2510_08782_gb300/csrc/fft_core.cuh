@@ -1,0 +1,124 @@
+// Mixed-radix Stockham FFT core shared by every pencil kernel (internal).
+//
+// The pseudo-spectral discretisation of Sec. 2.2 applies and inverts differential operators
+// with FFTs. Each CUDA kernel stages a batch of pencils in shared memory and runs this
+// self-sorting (Stockham) radix-2/3/4/5/8 transform on them. Stage s with radix R and span Ns
+// (product of the radices already applied) maps butterfly j of every pencil as
+//     v_r = x[j + r N/R] * W_N^{r (j mod Ns) N/(Ns R)},  v <- DFT_R(v),
+//     y[(j - j mod Ns) R + j mod Ns + r Ns] = v_r,
+// which is the classic out-of-place Stockham formulation; after the last stage the result is
+// in natural order. Forward transforms use W_N = exp(-2 pi i / N); an inverse transform is done
+// as conj(FFT(conj(x))). The functions are host+device so the same code is unit-tested on the CPU.
+#pragma once
+
+#include "common.cuh"
+
+namespace ga {
+
+// Mathematical constants of the small DFTs.
+#define GA_SQRT3_2 0.86602540378443864676
+#define GA_SQRT1_2 0.70710678118654752440
+#define GA_C1_5 0.30901699437494742410   /* cos(2 pi / 5) */
+#define GA_C2_5 (-0.80901699437494742410) /* cos(4 pi / 5) */
+#define GA_S1_5 0.95105651629515357212   /* sin(2 pi / 5) */
+#define GA_S2_5 0.58778525229247312917   /* sin(4 pi / 5) */
+
+template <typename C> GA_HD void dft2(C* a) {
+  C t = a[1];
+  a[1] = csub(a[0], t);
+  a[0] = cadd(a[0], t);
+}
+
+template <typename C> GA_HD void dft4(C* a) {
+  C t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+  C t2 = cadd(a[1], a[3]), t3 = cmul_negi(csub(a[1], a[3]));
+  a[0] = cadd(t0, t2);
+  a[2] = csub(t0, t2);
+  a[1] = cadd(t1, t3);
+  a[3] = csub(t1, t3);
+}
+
+template <typename T, typename C> GA_HD void dft3(C* a) {
+  const T c = T(-0.5), s = T(GA_SQRT3_2);
+  C sm = cadd(a[1], a[2]), df = csub(a[1], a[2]);
+  C base = cadd(a[0], cscale(sm, c));
+  C rot = cscale(cmul_negi(df), s);  // -i s (a1 - a2)
+  a[0] = cadd(a[0], sm);
+  a[1] = cadd(base, rot);
+  a[2] = csub(base, rot);
+}
+
+template <typename T, typename C> GA_HD void dft5(C* a) {
+  const T c1 = T(GA_C1_5), c2 = T(GA_C2_5), s1 = T(GA_S1_5), s2 = T(GA_S2_5);
+  C sa = cadd(a[1], a[4]), da = csub(a[1], a[4]);
+  C sb = cadd(a[2], a[3]), db = csub(a[2], a[3]);
+  C r1 = cadd(a[0], cadd(cscale(sa, c1), cscale(sb, c2)));
+  C r2 = cadd(a[0], cadd(cscale(sa, c2), cscale(sb, c1)));
+  C i1 = cmul_negi(cadd(cscale(da, s1), cscale(db, s2)));  // -i (s1 da + s2 db)
+  C i2 = cmul_negi(csub(cscale(da, s2), cscale(db, s1)));  // -i (s2 da - s1 db)
+  a[0] = cadd(a[0], cadd(sa, sb));
+  a[1] = cadd(r1, i1);
+  a[4] = csub(r1, i1);
+  a[2] = cadd(r2, i2);
+  a[3] = csub(r2, i2);
+}
+
+template <typename T, typename C> GA_HD void dft8(C* a) {
+  C e[4] = {a[0], a[2], a[4], a[6]};
+  C o[4] = {a[1], a[3], a[5], a[7]};
+  dft4(e);
+  dft4(o);
+  const T r = T(GA_SQRT1_2);
+  // twiddles W8^k, k = 0..3: 1, (r, -r), -i, (-r, -r)
+  C o1 = mk<T>((o[1].x + o[1].y) * r, (o[1].y - o[1].x) * r);
+  C o2 = cmul_negi(o[2]);
+  C o3 = mk<T>((o[3].y - o[3].x) * r, -(o[3].x + o[3].y) * r);
+  a[0] = cadd(e[0], o[0]);
+  a[4] = csub(e[0], o[0]);
+  a[1] = cadd(e[1], o1);
+  a[5] = csub(e[1], o1);
+  a[2] = cadd(e[2], o2);
+  a[6] = csub(e[2], o2);
+  a[3] = cadd(e[3], o3);
+  a[7] = csub(e[3], o3);
+}
+
+// One butterfly of one Stockham stage. `in`/`out` point at the start of the pencil.
+template <typename T>
+GA_HD void stockham_butterfly(const cx<T>* in, cx<T>* out, int j, int N, int R, int Ns,
+                              const cx<T>* tw) {
+  const int M = N / R;
+  const int k = j % Ns;
+  const int tstep = k * (N / (Ns * R));
+  cx<T> v[8];
+  v[0] = in[j];
+  for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * M], tw[r * tstep]);
+  switch (R) {
+    case 2: dft2(v); break;
+    case 3: dft3<T>(v); break;
+    case 4: dft4(v); break;
+    case 5: dft5<T>(v); break;
+    default: dft8<T>(v); break;
+  }
+  const int base = (j - k) * R + k;
+  for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+}
+
+// Host: factor N into radices (8s first for powers of two, then 4/2, 3, 5). Returns false if N
+// has a prime factor other than 2, 3, 5 or if N < 1.
+inline bool make_plan(int N, FftPlan* p) {
+  if (N < 1) return false;
+  p->n = N;
+  p->ns = 0;
+  int m = N;
+  int twos = 0;
+  while (m % 2 == 0) { m /= 2; ++twos; }
+  while (twos >= 3) { p->radix[p->ns++] = 8; twos -= 3; }
+  if (twos == 2) p->radix[p->ns++] = 4;
+  if (twos == 1) p->radix[p->ns++] = 2;
+  while (m % 3 == 0) { m /= 3; p->radix[p->ns++] = 3; }
+  while (m % 5 == 0) { m /= 5; p->radix[p->ns++] = 5; }
+  return m == 1 && p->ns < 24;
+}
+
+}  // namespace ga

@@ -1,0 +1,375 @@
+// Pencil FFT kernels: 1D spectral derivatives (fused with the body-force / divergence
+// accumulation) and the passes of the real 3D FFT (Sec. 2.2: "two FFTs and a diagonal scaling").
+//
+// Every kernel stages a batch of pencils of one axis in shared memory (padded leading dimension
+// to spread banks), runs the Stockham transform of fft_core.cuh, and writes back. Pencils along the
+// contiguous axis are whole rows; pencils along the other axes are tiles of adjacent columns, so
+// every global access is a contiguous row segment (coalesced). Two real pencils are packed into one
+// complex pencil (z = a + i b):
+//  * derivative: F^{-1}[i k~ F z] = d a + i d b exactly, because k~ is odd in k with the Nyquist
+//    entry zeroed, so the derivative of a real pencil is real;
+//  * real FFT rows: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i).
+// A 3D spectral derivative along one axis factorises into the 1D derivative along that axis (the
+// transforms of the other axes cancel), so d/dx_c costs one pass, not a 3D FFT.
+#include <cuda_runtime.h>
+
+#include "fft_core.cuh"
+#include "kernels.h"
+
+namespace ga {
+
+namespace {
+
+template <typename T>
+__device__ cx<T>* run_fft(cx<T>* a, cx<T>* b, int N, int B, int ld, const FftPlan& plan,
+                          const cx<T>* tw) {
+  int Ns = 1;
+  for (int s = 0; s < plan.ns; ++s) {
+    const int R = plan.radix[s];
+    const int M = N / R;
+    const int total = B * M;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int p = t / M;
+      const int j = t - p * M;
+      stockham_butterfly<T>(a + p * ld, b + p * ld, j, N, R, Ns, tw);
+    }
+    __syncthreads();
+    cx<T>* tmp = a;
+    a = b;
+    b = tmp;
+    Ns *= R;
+  }
+  return a;
+}
+
+// derivative wavenumber k~ of FFT index j of a length-L axis (zero at the Nyquist index)
+template <typename T> __device__ __forceinline__ T ktilde(int j, int L) {
+  if (2 * j == L) return T(0);
+  return (2 * j < L) ? T(j) : T(j - L);
+}
+
+// conj(i k~ z) rotated for the conj-FFT-conj inverse: (-k~ z.y, -k~ z.x)
+template <typename T> __device__ __forceinline__ void mult_ik_conj(cx<T>* r, int B, int L, int ld) {
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+    const int p = idx / L, j = idx - p * L;
+    const T kt = ktilde<T>(j, L);
+    const cx<T> z = r[p * ld + j];
+    r[p * ld + j] = mk<T>(-kt * z.y, -kt * z.x);
+  }
+  __syncthreads();
+}
+
+template <typename T> __device__ __forceinline__ void load_tw(cx<T>* tw, const cx<T>* twg, int L) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+}
+
+// ---- derivative along the contiguous axis (rows) --------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
+             int accumulate, long long rows, int L, int B, int ld, FftPlan plan,
+             const cx<T>* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* a = tw + L;
+  cx<T>* b = a + B * ld;
+  load_tw<T>(tw, twg, L);
+  const long long row0 = (long long)blockIdx.x * 2 * B;
+  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
+    const int rr = idx / L, j = idx - rr * L;
+    const long long row = row0 + rr;
+    const T val = row < rows ? f[row * L + j] : T(0);
+    reinterpret_cast<T*>(&a[(rr >> 1) * ld + j])[rr & 1] = val;
+  }
+  __syncthreads();
+  cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  cx<T>* o = (r == a) ? b : a;
+  mult_ik_conj<T>(r, B, L, ld);
+  cx<T>* r2 = run_fft<T>(r, o, L, B, ld, plan, tw);
+  const T inv = T(1) / T(L);
+  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
+    const int rr = idx / L, j = idx - rr * L;
+    const long long row = row0 + rr;
+    if (row >= rows) continue;
+    const cx<T> z = r2[(rr >> 1) * ld + j];
+    const T d = (rr & 1) ? -z.y * inv : z.x * inv;
+    const long long oi = row * L + j;
+    T val = coef * d;
+    if (mult) val *= mult[oi];
+    out[oi] = accumulate ? out[oi] + val : val;
+  }
+}
+
+// ---- derivative along a strided axis (tiles of 2B adjacent columns) ---------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
+             int accumulate, int L, long long S, long long outer_stride, int nx, int B, int ld,
+             FftPlan plan, const cx<T>* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* a = tw + L;
+  cx<T>* b = a + B * ld;
+  load_tw<T>(tw, twg, L);
+  const int x0 = blockIdx.x * 2 * B;
+  const long long base = (long long)blockIdx.y * outer_stride + x0;
+  const int W = 2 * B;
+  for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
+    const int j = idx / W, xx = idx - j * W;
+    const T val = (x0 + xx < nx) ? f[base + j * S + xx] : T(0);
+    reinterpret_cast<T*>(&a[(xx >> 1) * ld + j])[xx & 1] = val;
+  }
+  __syncthreads();
+  cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  cx<T>* o = (r == a) ? b : a;
+  mult_ik_conj<T>(r, B, L, ld);
+  cx<T>* r2 = run_fft<T>(r, o, L, B, ld, plan, tw);
+  const T inv = T(1) / T(L);
+  for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
+    const int j = idx / W, xx = idx - j * W;
+    if (x0 + xx >= nx) continue;
+    const cx<T> z = r2[(xx >> 1) * ld + j];
+    const T d = (xx & 1) ? -z.y * inv : z.x * inv;
+    const long long oi = base + j * S + xx;
+    T val = coef * d;
+    if (mult) val *= mult[oi];
+    out[oi] = accumulate ? out[oi] + val : val;
+  }
+}
+
+// ---- real-to-complex FFT of row pairs ---------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_r2c_rows(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, int L, int Lh, int B,
+           int ld, FftPlan plan, const cx<T>* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* a = tw + L;
+  cx<T>* b = a + B * ld;
+  load_tw<T>(tw, twg, L);
+  const long long row0 = (long long)blockIdx.x * 2 * B;
+  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
+    const int rr = idx / L, j = idx - rr * L;
+    const long long row = row0 + rr;
+    const T val = row < rows ? f[row * L + j] : T(0);
+    reinterpret_cast<T*>(&a[(rr >> 1) * ld + j])[rr & 1] = val;
+  }
+  __syncthreads();
+  const cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  for (int idx = threadIdx.x; idx < B * Lh; idx += blockDim.x) {
+    const int p = idx / Lh, k = idx - p * Lh;
+    const cx<T> zk = r[p * ld + k];
+    const cx<T> zm = cconj(r[p * ld + (k == 0 ? 0 : L - k)]);
+    const cx<T> A = cscale(cadd(zk, zm), T(0.5));
+    const cx<T> Bv = cscale(cmul_negi(csub(zk, zm)), T(0.5));
+    const long long ra = row0 + 2 * p;
+    if (ra < rows) fh[ra * Lh + k] = A;
+    if (ra + 1 < rows) fh[(ra + 1) * Lh + k] = Bv;
+  }
+}
+
+// ---- complex-to-real inverse FFT of row pairs (normalised by `scale`) --------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_c2r_rows(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, int L, int Lh, int B,
+           int ld, FftPlan plan, const cx<T>* __restrict__ twg, T scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* a = tw + L;
+  cx<T>* b = a + B * ld;
+  load_tw<T>(tw, twg, L);
+  const long long row0 = (long long)blockIdx.x * 2 * B;
+  for (int idx = threadIdx.x; idx < 2 * B * Lh; idx += blockDim.x) {
+    const int rr = idx / Lh, k = idx - rr * Lh;
+    const long long row = row0 + rr;
+    const cx<T> val = row < rows ? fh[row * Lh + k] : mk<T>(T(0), T(0));
+    ((rr & 1) ? b : a)[(rr >> 1) * ld + k] = val;
+  }
+  __syncthreads();
+  // Z_k = A_k + i B_k (k < Lh) and Z_{L-k} = conj(A_k) + i conj(B_k); store conj(Z) in `a`.
+  for (int idx = threadIdx.x; idx < B * Lh; idx += blockDim.x) {
+    const int p = idx / Lh, k = idx - p * Lh;
+    const cx<T> A = a[p * ld + k], Bv = b[p * ld + k];
+    const cx<T> z = mk<T>(A.x - Bv.y, A.y + Bv.x);
+    a[p * ld + k] = cconj(z);
+    if (k >= 1 && L - k >= Lh) {
+      const cx<T> zm = mk<T>(A.x + Bv.y, -A.y + Bv.x);  // conj(A) + i conj(B)
+      a[p * ld + L - k] = cconj(zm);
+    }
+  }
+  __syncthreads();
+  const cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
+    const int rr = idx / L, j = idx - rr * L;
+    const long long row = row0 + rr;
+    if (row >= rows) continue;
+    const cx<T> z = r[(rr >> 1) * ld + j];
+    f[row * L + j] = ((rr & 1) ? -z.y : z.x) * scale;
+  }
+}
+
+// ---- complex FFT along a strided axis of the half spectrum, in place ---------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_fft_cols(cx<T>* __restrict__ fh, int L, long long S, long long outer_stride, int nx, int B, int ld,
+           FftPlan plan, const cx<T>* __restrict__ twg, int inverse, T scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* a = tw + L;
+  cx<T>* b = a + B * ld;
+  load_tw<T>(tw, twg, L);
+  const int x0 = blockIdx.x * B;
+  const long long base = (long long)blockIdx.y * outer_stride + x0;
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+    const int j = idx / B, p = idx - j * B;
+    cx<T> z = (x0 + p < nx) ? fh[base + j * S + p] : mk<T>(T(0), T(0));
+    if (inverse) z = cconj(z);
+    a[p * ld + j] = z;
+  }
+  __syncthreads();
+  const cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+    const int j = idx / B, p = idx - j * B;
+    if (x0 + p >= nx) continue;
+    cx<T> z = r[p * ld + j];
+    if (inverse) z = cscale(cconj(z), scale);
+    fh[base + j * S + p] = z;
+  }
+}
+
+// pencils per CTA: about 4096 complex fp32 (2048 fp64) values per buffer
+template <typename T> int batch_for(int L) {
+  const int target = sizeof(T) == 4 ? 4096 : 2048;
+  int B = target / L;
+  return B < 1 ? 1 : B;
+}
+inline int lead_dim(int L) { return (L % 2 == 0) ? L + 1 : L; }
+template <typename T> size_t smem_bytes(int L, int B) {
+  return sizeof(cx<T>) * ((size_t)L + 2 * (size_t)B * lead_dim(L));
+}
+
+template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult,
+                         T* out, T coef, bool accumulate, cudaStream_t st) {
+  const int L = g.n[axis];
+  if (L == 1) {  // a singleton axis carries only k = 0: the derivative is zero
+    if (accumulate) return cudaSuccess;
+    return cudaMemsetAsync(out, 0, sizeof(T) * g.nvox, st);
+  }
+  int B = batch_for<T>(L);
+  const int ld = lead_dim(L);
+  if (axis == 2) {
+    const long long rows = (long long)g.n[0] * g.n[1];
+    const long long pairs = (rows + 1) / 2;
+    if (B > pairs) B = (int)pairs;
+    const size_t sm = smem_bytes<T>(L, B);
+    cudaError_t e = allow_smem(k_deriv_rows<T>, sm);
+    if (e != cudaSuccess) return e;
+    const long long grid = (rows + 2LL * B - 1) / (2LL * B);
+    k_deriv_rows<T><<<(unsigned)grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, rows,
+                                                           L, B, ld, ft.plan[2], ft.tw[2]);
+    return cudaGetLastError();
+  }
+  const int nx = g.n[2];
+  if (2 * B > nx) B = (nx + 1) / 2;
+  const size_t sm = smem_bytes<T>(L, B);
+  cudaError_t e = allow_smem(k_deriv_cols<T>, sm);
+  if (e != cudaSuccess) return e;
+  long long S, outer_stride;
+  int outer;
+  if (axis == 1) {
+    S = nx;
+    outer = g.n[0];
+    outer_stride = (long long)g.n[1] * nx;
+  } else {
+    S = (long long)g.n[1] * nx;
+    outer = g.n[1];
+    outer_stride = nx;
+  }
+  dim3 grid((nx + 2 * B - 1) / (2 * B), outer);
+  k_deriv_cols<T><<<grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, L, S, outer_stride,
+                                               nx, B, ld, ft.plan[axis], ft.tw[axis]);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_cols(const Grid& g, const FftTables<T>& ft, int axis, cx<T>* fh, int inverse,
+                               cudaStream_t st) {
+  const int L = g.n[axis];
+  if (L == 1) return cudaSuccess;
+  const int nx = g.n2h;
+  int B = batch_for<T>(L);
+  if (B > nx) B = nx;
+  const int ld = lead_dim(L);
+  const size_t sm = smem_bytes<T>(L, B);
+  cudaError_t e = allow_smem(k_fft_cols<T>, sm);
+  if (e != cudaSuccess) return e;
+  long long S, outer_stride;
+  int outer;
+  if (axis == 1) {
+    S = nx;
+    outer = g.n[0];
+    outer_stride = (long long)g.n[1] * nx;
+  } else {
+    S = (long long)g.n[1] * nx;
+    outer = g.n[1];
+    outer_stride = nx;
+  }
+  dim3 grid((nx + B - 1) / B, outer);
+  k_fft_cols<T><<<grid, kThreads, sm, st>>>(fh, L, S, outer_stride, nx, B, ld, ft.plan[axis], ft.tw[axis],
+                                             inverse, T(1) / T(L));
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_r2c(const Grid& g, const FftTables<T>& ft, const T* f, cx<T>* fh, cudaStream_t st) {
+  const int L = g.n[2];
+  const long long rows = (long long)g.n[0] * g.n[1];
+  int B = batch_for<T>(L);
+  if (B > (rows + 1) / 2) B = (int)((rows + 1) / 2);
+  const int ld = lead_dim(L);
+  const size_t sm = smem_bytes<T>(L, B);
+  cudaError_t e = allow_smem(k_r2c_rows<T>, sm);
+  if (e != cudaSuccess) return e;
+  const long long grid = (rows + 2LL * B - 1) / (2LL * B);
+  k_r2c_rows<T><<<(unsigned)grid, kThreads, sm, st>>>(f, fh, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2]);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_cols<T>(g, ft, 1, fh, 0, st)) != cudaSuccess) return e;
+  return launch_cols<T>(g, ft, 0, fh, 0, st);
+}
+
+template <typename T>
+cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_cols<T>(g, ft, 0, fh, 1, st)) != cudaSuccess) return e;
+  if ((e = launch_cols<T>(g, ft, 1, fh, 1, st)) != cudaSuccess) return e;
+  const int L = g.n[2];
+  const long long rows = (long long)g.n[0] * g.n[1];
+  int B = batch_for<T>(L);
+  if (B > (rows + 1) / 2) B = (int)((rows + 1) / 2);
+  const int ld = lead_dim(L);
+  const size_t sm = smem_bytes<T>(L, B);
+  if ((e = allow_smem(k_c2r_rows<T>, sm)) != cudaSuccess) return e;
+  const long long grid = (rows + 2LL * B - 1) / (2LL * B);
+  k_c2r_rows<T><<<(unsigned)grid, kThreads, sm, st>>>(fh, f, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2],
+                                                       T(1) / T(L));
+  return cudaGetLastError();
+}
+
+#define GA_INST(T)                                                                                  \
+  template cudaError_t launch_deriv<T>(const Grid&, const FftTables<T>&, int, const T*, const T*, T*, T, \
+                                       bool, cudaStream_t);                                          \
+  template cudaError_t launch_r2c<T>(const Grid&, const FftTables<T>&, const T*, cx<T>*, cudaStream_t); \
+  template cudaError_t launch_c2r<T>(const Grid&, const FftTables<T>&, cx<T>*, T*, cudaStream_t);
+GA_INST(float)
+GA_INST(double)
+#undef GA_INST
+
+}  // namespace ga

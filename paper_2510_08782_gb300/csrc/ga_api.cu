@@ -1,0 +1,991 @@
+// Runtime behind the C ABI of include/ga.h and include/ga_ops.h.
+//
+// One context owns every device buffer of one problem and orders all work on one stream. The
+// gradient evaluation (Eq. (3)) runs as: spectral prologue (F v, regulariser value, mu = div v by
+// 1D derivative passes), RK2 departure points, n_t state steps (all states or checkpoints every K),
+// mismatch and terminal adjoint value, then backwards in time the body force
+// h_t w_j lambda_j grad m_j (one fused FFT-derivative pass per axis) and the adjoint step, and the
+// spectral epilogue g^ = alpha L^ v^ + (P) b^ (optionally fused with s^ = -(P g^)/(alpha L^)).
+// The solver (Alg. 3) drives the line search from the host: each Armijo trial is a state solve whose
+// FP64 objective is read back; the window inner products, the Gram update, the least-squares solve
+// and the combination run on the device.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/ga.h"
+#include "../../include/ga_ops.h"
+#include "fft_core.cuh"
+#include "kernels.h"
+
+using namespace ga;
+
+namespace {
+
+constexpr int kNumRes = 64;  // device FP64 result slots
+
+struct Fail {
+  ga_status st;
+};
+
+}  // namespace
+
+struct EngineBase {
+  virtual ~EngineBase() {}
+};
+
+template <typename T> struct Engine;
+
+struct ga_ctx {
+  ga_problem_desc desc;
+  ga_solver_opts opts;
+  cudaStream_t st = nullptr;
+  std::string err;
+  ga_stats stats;
+  int prec = 0;
+  Engine<float>* ef = nullptr;
+  Engine<double>* ed = nullptr;
+};
+
+namespace {
+
+void set_err(ga_ctx* c, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+}
+
+}  // namespace
+
+template <typename T> struct Engine : EngineBase {
+  ga_ctx* ctx;
+  Grid g;
+  int dim, nt, model, s, K;
+  double alpha, ht, hd;
+  long long nv, vl;
+  cudaStream_t st;
+  FftTables<T> ft;
+  std::vector<void*> allocs;
+  void* pinned = nullptr;
+  double* hres = nullptr;
+
+  T *m0 = nullptr, *m1 = nullptr, *xm = nullptr, *xp = nullptr, *mu = nullptr;
+  T *lam[2] = {nullptr, nullptr}, *body = nullptr, *tmp[2] = {nullptr, nullptr};
+  T *states = nullptr, *seg = nullptr, *io_a = nullptr, *io_b = nullptr;
+  int nslots = 0, seg_base = -1;
+  cx<T> *vh = nullptr, *bh = nullptr;
+  double *dpart = nullptr, *dres = nullptr, *dM = nullptr, *dbeta = nullptr;
+
+  // solver state
+  int W1 = 1;
+  std::vector<T*> vfree, gfree;
+  std::deque<std::pair<T*, T*>> win;  // (v, g), newest first
+  T* S = nullptr;                      // preconditioned direction at the current iterate
+  bool s_valid = false, started = false;
+  int k = 0;
+  double g0inf = 0.0, J = 0.0, mis = 0.0, rho_mem = 1.0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+
+  // profiling of one kernel class with events (see ga_prof_start)
+  int prof_class = -1;
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_used = 0;
+  double prof_ms = 0.0;
+  long long prof_launches = 0;
+
+  ~Engine() override {
+    for (void* p : allocs) cudaFree(p);
+    if (pinned) cudaFreeHost(pinned);
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    for (auto e : prof_ev) cudaEventDestroy(e);
+  }
+
+  void ck(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+      set_err(ctx, "%s: %s", what, cudaGetErrorString(e));
+      throw Fail{e == cudaErrorMemoryAllocation ? GA_ERR_NOMEM : GA_ERR_CUDA};
+    }
+  }
+  template <typename U> U* dalloc(long long count) {
+    void* p = nullptr;
+    if (count < 1) count = 1;
+    cudaError_t e = cudaMalloc(&p, sizeof(U) * (size_t)count);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_err(ctx, "cudaMalloc of %lld bytes failed: %s", (long long)(sizeof(U) * count), cudaGetErrorString(e));
+      throw Fail{GA_ERR_NOMEM};
+    }
+    allocs.push_back(p);
+    return static_cast<U*>(p);
+  }
+
+  void init(ga_ctx* c, const void* hm0, const void* hm1, int mem) {
+    ctx = c;
+    st = c->st;
+    const ga_problem_desc& d = c->desc;
+    dim = d.dim;
+    nt = d.nt;
+    model = d.model;
+    s = d.reg_order;
+    alpha = d.alpha;
+    K = d.ckpt_every;
+    g.dim = dim;
+    if (dim == 3) {
+      g.n[0] = d.n[0];
+      g.n[1] = d.n[1];
+      g.n[2] = d.n[2];
+    } else {
+      g.n[0] = 1;
+      g.n[1] = d.n[0];
+      g.n[2] = d.n[1];
+    }
+    g.n2h = g.n[2] / 2 + 1;
+    g.nvox = (long long)g.n[0] * g.n[1] * g.n[2];
+    g.nhalf = (long long)g.n[0] * g.n[1] * g.n2h;
+    nv = g.nvox;
+    vl = nv * dim;
+    ht = 1.0 / nt;
+    hd = 1.0;
+    for (int a = 3 - dim; a < 3; ++a) hd *= 2.0 * M_PI / g.n[a];
+    ck(cudaEventCreate(&ev[0]), "cudaEventCreate");
+    ck(cudaEventCreate(&ev[1]), "cudaEventCreate");
+
+    // FFT plans and twiddle tables per internal axis
+    for (int a = 0; a < 3; ++a) {
+      make_plan(g.n[a], &ft.plan[a]);
+      const int L = g.n[a];
+      std::vector<cx<T>> tw(L);
+      for (int m = 0; m < L; ++m) {
+        // angle -2 pi m / L, reduced to the first octants for accuracy
+        const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m / L;
+        tw[m] = mk<T>((T)cosl(ang), (T)sinl(ang));
+      }
+      cx<T>* dtw = dalloc<cx<T>>(L);
+      ck(cudaMemcpy(dtw, tw.data(), sizeof(cx<T>) * L, cudaMemcpyHostToDevice), "twiddle upload");
+      ft.tw[a] = dtw;
+    }
+
+    m0 = dalloc<T>(nv);
+    m1 = dalloc<T>(nv);
+    const cudaMemcpyKind kind = mem == GA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    ck(cudaMemcpyAsync(m0, hm0, sizeof(T) * nv, kind, st), "copy m0");
+    ck(cudaMemcpyAsync(m1, hm1, sizeof(T) * nv, kind, st), "copy m1");
+    xm = dalloc<T>(vl);
+    xp = dalloc<T>(vl);
+    mu = dalloc<T>(nv);
+    lam[0] = dalloc<T>(nv);
+    lam[1] = dalloc<T>(nv);
+    tmp[0] = dalloc<T>(nv);
+    tmp[1] = dalloc<T>(nv);
+    body = dalloc<T>(vl);
+    io_a = dalloc<T>(vl);
+    io_b = dalloc<T>(vl);
+    nslots = (K == 0) ? nt : (nt / K + (nt % K != 0 ? 1 : 0));
+    states = dalloc<T>((long long)nslots * nv);
+    if (K > 1) seg = dalloc<T>((long long)(K - 1) * nv);
+    vh = dalloc<cx<T>>(g.nhalf * dim);
+    bh = dalloc<cx<T>>(g.nhalf * dim);
+    dpart = dalloc<double>((long long)kMaxDots * kRedBlocks);
+    dres = dalloc<double>(kNumRes);
+    ck(cudaMallocHost(&pinned, sizeof(double) * kNumRes), "cudaMallocHost");
+    hres = static_cast<double*>(pinned);
+
+    // solver pools: window (w+1) + trial q + one more, for iterates and gradients
+    W1 = c->opts.window + 1;
+    for (int i = 0; i < W1 + 2; ++i) {
+      vfree.push_back(dalloc<T>(vl));
+      gfree.push_back(dalloc<T>(vl));
+    }
+    S = dalloc<T>(vl);
+    dM = dalloc<double>((long long)W1 * W1);
+    dbeta = dalloc<double>(kMaxWin + 4);
+    ck(cudaMemsetAsync(dM, 0, sizeof(double) * W1 * W1, st), "memset");
+    ck(cudaStreamSynchronize(st), "setup sync");
+  }
+
+  // ---- profiling hooks ------------------------------------------------------------------------
+  enum { PROF_SL = 0, PROF_DERIV = 1, PROF_FFT = 2 };
+  void prof_begin(int cls) {
+    if (prof_class != cls) return;
+    if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
+    ck(cudaEventRecord(prof_ev[prof_used], st), "cudaEventRecord");
+  }
+  void prof_end(int cls) {
+    if (prof_class != cls) return;
+    ck(cudaEventRecord(prof_ev[prof_used + 1], st), "cudaEventRecord");
+    prof_used += 2;
+    ++prof_launches;
+  }
+  void prof_flush() {
+    if (prof_used == 0) return;
+    ck(cudaEventSynchronize(prof_ev[prof_used - 1]), "cudaEventSynchronize");
+    for (int i = 0; i < prof_used; i += 2) {
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, prof_ev[i], prof_ev[i + 1]), "cudaEventElapsedTime");
+      prof_ms += ms;
+    }
+    prof_used = 0;
+  }
+
+  // ---- building blocks --------------------------------------------------------------------------
+  const T* slot(int j) const {
+    if (j == 0) return m0;
+    if (K == 0) return states + (long long)(j - 1) * nv;
+    if (j % K == 0) return states + (long long)(j / K - 1) * nv;
+    return states + (long long)(nt / K) * nv;  // the final state when K does not divide n_t
+  }
+  bool stored(int j) const { return K == 0 || j % K == 0 || j == nt; }
+
+  void sl_forward(const T* src, T* dst) {
+    prof_begin(PROF_SL);
+    ck(launch_sl_forward<T>(g, model == GA_MODEL_CONTINUITY, src, xm, mu, dst, (T)ht, st), "sl_forward");
+    prof_end(PROF_SL);
+  }
+  void sl_adjoint(const T* src, T* dst) {
+    prof_begin(PROF_SL);
+    ck(launch_sl_adjoint<T>(g, model == GA_MODEL_CONTINUITY, src, xp, mu, dst, (T)ht, st), "sl_adjoint");
+    prof_end(PROF_SL);
+  }
+  void deriv(int axis, const T* f, const T* mult, T* out, double coef, bool acc) {
+    prof_begin(PROF_DERIV);
+    ck(launch_deriv<T>(g, ft, axis, f, mult, out, (T)coef, acc, st), "deriv");
+    prof_end(PROF_DERIV);
+  }
+  void r2c(const T* f, cx<T>* fh) {
+    prof_begin(PROF_FFT);
+    ck(launch_r2c<T>(g, ft, f, fh, st), "r2c");
+    prof_end(PROF_FFT);
+  }
+  void c2r(cx<T>* fh, T* f) {
+    prof_begin(PROF_FFT);
+    ck(launch_c2r<T>(g, ft, fh, f, st), "c2r");
+    prof_end(PROF_FFT);
+  }
+
+  void compute_mu(const T* v) {
+    for (int c = 0; c < dim; ++c) deriv(g.axis_of(c), v + c * nv, nullptr, mu, 1.0, c > 0);
+  }
+  bool needs_mu_forward() const { return model == GA_MODEL_CONTINUITY; }
+  bool needs_mu_adjoint() const { return model != GA_MODEL_CONTINUITY; }
+
+  // F v into vh and the regulariser sum into dres[slot]
+  void prologue(const T* v, int res_slot) {
+    for (int c = 0; c < dim; ++c) r2c(v + c * nv, vh + c * g.nhalf);
+    ck(launch_reg_sum<T>(g, s, vh, dpart, st), "reg_sum");
+    ck(launch_sum_partials(dpart, 1, kRedBlocks, dres + res_slot, st), "sum");
+  }
+  double reg_value(double raw) const { return 0.5 * alpha * hd / (double)nv * raw; }
+
+  // State solve keeping only the final state; returns pointer to m(1).
+  const T* forward_final(const T* v) {
+    ck(launch_departure<T>(g, v, xm, xp, (T)ht, st), "departure");
+    const T* cur = m0;
+    for (int j = 0; j < nt; ++j) {
+      T* dst = tmp[(j + 1) & 1];
+      sl_forward(cur, dst);
+      cur = dst;
+    }
+    return cur;
+  }
+
+  void forward_all() {
+    const T* cur = m0;
+    for (int j = 0; j < nt; ++j) {
+      T* dst = stored(j + 1) ? const_cast<T*>(slot(j + 1)) : tmp[(j + 1) & 1];
+      sl_forward(cur, dst);
+      cur = dst;
+    }
+    seg_base = -1;
+  }
+
+  const T* state(int j) {
+    if (stored(j)) return slot(j);
+    const int js = (j / K) * K;
+    if (seg_base != js) {
+      const T* cur = slot(js);
+      const int last = (js + K - 1 < nt - 1) ? js + K - 1 : nt - 1;
+      for (int i = js + 1; i <= last; ++i) {
+        T* dst = seg + (long long)(i - js - 1) * nv;
+        sl_forward(cur, dst);
+        cur = dst;
+      }
+      seg_base = js;
+    }
+    return seg + (long long)(j - js - 1) * nv;
+  }
+
+  void read_results(int count) {
+    ck(cudaMemcpyAsync(hres, dres, sizeof(double) * count, cudaMemcpyDeviceToHost, st), "result copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    prof_flush();
+  }
+
+  // obj(v): one state solve. Results: dres[0] = sum (m(1) - m1)^2, dres[1] = regulariser sum.
+  double objective(const T* v, double* mismatch = nullptr) {
+    ck(cudaEventRecord(ev[0], st), "event");
+    prologue(v, 1);
+    if (needs_mu_forward()) compute_mu(v);
+    const T* mT = forward_final(v);
+    ck(launch_mismatch<T>(mT, m1, nullptr, nv, dpart, dres, st), "mismatch");
+    ck(cudaEventRecord(ev[1], st), "event");
+    read_results(2);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ctx->stats.t_obj_ms += ms;
+    ctx->stats.obj_evals += 1;
+    ctx->stats.pde_solves += 1;
+    const double m = 0.5 * hd * hres[0];
+    if (mismatch) *mismatch = m;
+    return m + reg_value(hres[1]);
+  }
+
+  // Body force b (not projected) from the adjoint started at lam_init (lam_init may be lam[0]).
+  // Requires departure points, mu and the forward states.
+  void body_force(const T* lam_init) {
+    ck(cudaMemsetAsync(body, 0, sizeof(T) * vl, st), "memset body");
+    const T* lcur = lam_init;
+    int pp = (lam_init == lam[0]) ? 1 : 0;
+    for (int j = nt; j >= 0; --j) {
+      const T* mj = state(j);
+      const double coef = ht * ((j == 0 || j == nt) ? 0.5 : 1.0);
+      for (int c = 0; c < dim; ++c) {
+        if (model == GA_MODEL_CONTINUITY)
+          deriv(g.axis_of(c), lcur, mj, body + c * nv, -coef, true);
+        else
+          deriv(g.axis_of(c), mj, lcur, body + c * nv, coef, true);
+      }
+      if (j > 0) {
+        T* ldst = lam[pp];
+        sl_adjoint(lcur, ldst);
+        lcur = ldst;
+        pp ^= 1;
+      }
+    }
+  }
+
+  // Reduced gradient; writes g (vl) and, when s_out != nullptr, s = -(alpha L)^{-1} (P) g.
+  double gradient(const T* v, T* gout, T* s_out, double* mismatch = nullptr) {
+    ck(cudaEventRecord(ev[0], st), "event");
+    prologue(v, 1);
+    compute_mu(v);
+    ck(launch_departure<T>(g, v, xm, xp, (T)ht, st), "departure");
+    forward_all();
+    ck(launch_mismatch<T>(slot(nt), m1, lam[0], nv, dpart, dres, st), "mismatch");
+    body_force(lam[0]);
+    for (int c = 0; c < dim; ++c) r2c(body + c * nv, bh + c * g.nhalf);
+    SpecArgs sa{SPEC_EPILOGUE, s, alpha, model == GA_MODEL_INCOMPRESSIBLE ? 1 : 0, s_out ? 1 : 0};
+    ck(launch_spectral<T>(g, sa, bh, vh, st), "spectral epilogue");
+    for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, gout + c * nv);
+    if (s_out)
+      for (int c = 0; c < dim; ++c) c2r(vh + c * g.nhalf, s_out + c * nv);
+    ck(launch_maxabs<T>(gout, vl, dpart, dres + 2, st), "maxabs");
+    ck(cudaEventRecord(ev[1], st), "event");
+    read_results(3);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ctx->stats.t_grad_ms += ms;
+    ctx->stats.grad_evals += 1;
+    ctx->stats.pde_solves += 2;
+    const double m = 0.5 * hd * hres[0];
+    if (mismatch) *mismatch = m;
+    const double val = m + reg_value(hres[1]);
+    if (!std::isfinite(val) || !std::isfinite(hres[2])) {
+      set_err(ctx, "non-finite objective or gradient (obj=%g, |g|inf=%g)", val, hres[2]);
+      throw Fail{GA_ERR_NAN};
+    }
+    last_ginf = hres[2];
+    return val;
+  }
+  double last_ginf = 0.0;
+
+  void precond(const T* gin, T* sout) {
+    for (int c = 0; c < dim; ++c) r2c(gin + c * nv, bh + c * g.nhalf);
+    SpecArgs sa{SPEC_PRECOND, s, alpha, model == GA_MODEL_INCOMPRESSIBLE ? 1 : 0, 0};
+    ck(launch_spectral<T>(g, sa, bh, nullptr, st), "spectral precond");
+    for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, sout + c * nv);
+  }
+
+  double dot_l2(const T* a, const T* b) {
+    const T* bl[1] = {b};
+    ck(launch_dots<T>(a, bl, 1, vl, dpart, dres + 8, st), "dots");
+    read_results(9);
+    return hd * hres[8];
+  }
+
+  // ---- solver (Alg. 3) -----------------------------------------------------------------------------
+  void reset() {
+    while (!win.empty()) {
+      vfree.push_back(win.back().first);
+      gfree.push_back(win.back().second);
+      win.pop_back();
+    }
+    started = false;
+    s_valid = false;
+    k = 0;
+    rho_mem = 1.0;
+    g0inf = 0.0;
+    ctx->stats = ga_stats{};
+    ctx->stats.rho_mem = 1.0;
+  }
+
+  T* take(std::vector<T*>& pool) {
+    T* p = pool.back();
+    pool.pop_back();
+    return p;
+  }
+
+  // Append (v, g) as the newest window entry; update the device Gram of the window gradients.
+  void push_window(T* v, T* gv) {
+    int keep = (int)win.size();
+    if (keep == W1) {
+      vfree.push_back(win.back().first);
+      gfree.push_back(win.back().second);
+      win.pop_back();
+      keep = W1 - 1;
+    }
+    std::vector<const T*> bl;
+    bl.push_back(gv);
+    for (int i = 0; i < keep; ++i) bl.push_back(win[i].second);
+    ck(launch_dots<T>(gv, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "window dots");
+    ck(launch_gram_push(dM, W1, keep, dres + 16, st), "gram push");
+    win.push_front({v, gv});
+  }
+
+  bool is_fp_step(int kk) const {
+    const ga_solver_opts& o = ctx->opts;
+    if (o.method == GA_METHOD_RPGD) return true;
+    const int per = o.sigma + o.tau;
+    return o.variant == 2 ? (kk % per) < o.tau : (kk % per) >= o.sigma;
+  }
+
+  void start(const T* v0) {
+    reset();
+    T* v = take(vfree);
+    T* gv = take(gfree);
+    ck(cudaMemcpyAsync(v, v0, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy v0");
+    J = gradient(v, gv, S, &mis);
+    s_valid = true;
+    g0inf = last_ginf;
+    push_window(v, gv);
+    started = true;
+    ga_stats& stt = ctx->stats;
+    stt.obj = J;
+    stt.mismatch = mis;
+    stt.grad_inf0 = g0inf;
+    stt.rel_grad_inf = g0inf > 0 ? 1.0 : 0.0;
+    stt.rho_mem = rho_mem;
+  }
+
+  // One iteration k of Alg. 3. The current iterate is the newest window entry.
+  void step() {
+    const ga_solver_opts& o = ctx->opts;
+    ga_stats& stt = ctx->stats;
+    T* v = win.front().first;
+    T* gv = win.front().second;
+    if (!s_valid) precond(gv, S);
+    // Armijo line search with step memory (Eqs. (6)-(7), Sec. 2.3)
+    const double gs = dot_l2(gv, S);
+    T* q = take(vfree);
+    double rho = rho_mem, Jq = 0.0;
+    bool ok = false;
+    for (int it = 0; it <= o.max_backtracks; ++it) {
+      ck(launch_axpy<T>(q, v, S, rho, vl, st), "axpy");
+      Jq = objective(q);
+      stt.ls_trials += 1;
+      if (Jq < J + o.armijo_c * rho * gs) {
+        rho_mem = (it == 0) ? 2.0 * rho : rho;
+        ok = true;
+        break;
+      }
+      rho *= 0.5;
+    }
+    if (!ok) {
+      vfree.push_back(q);
+      set_err(ctx, "Armijo line search failed after %d halvings (iteration %d)", o.max_backtracks, k);
+      throw Fail{GA_ERR_LINESEARCH};
+    }
+    stt.last_rho = rho;
+    stt.rho_mem = rho_mem;
+    const bool fp = is_fp_step(k);
+    T* gq = take(gfree);
+    T *vn, *gn;
+    double Jn, misn;
+    if (fp) {
+      Jn = gradient(q, gq, S, &misn);
+      vn = q;
+      gn = gq;
+    } else {
+      double misq;
+      gradient(q, gq, nullptr, &misq);
+      const int m = (int)win.size();  // w^(k) + 1 window entries
+      std::vector<const T*> bl;
+      bl.push_back(gq);
+      for (int i = 0; i < m; ++i) bl.push_back(win[i].second);
+      ck(launch_dots<T>(gq, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "lsq dots");
+      ck(launch_lsq(m, dres + 16, dM, W1, dbeta, dres + 56, st), "lsq");
+      vn = take(vfree);
+      std::vector<const T*> vlst;
+      for (int i = 0; i < m; ++i) vlst.push_back(win[i].first);
+      ck(launch_combine<T>(vn, q, vlst.data(), dbeta, m, vl, st), "combine");
+      vfree.push_back(q);
+      gfree.push_back(gq);
+      gn = take(gfree);
+      Jn = gradient(vn, gn, S, &misn);
+    }
+    s_valid = true;
+    push_window(vn, gn);
+    J = Jn;
+    ++k;
+    stt.iters = k;
+    stt.last_branch = fp ? 1 : 0;
+    stt.obj = Jn;
+    stt.mismatch = misn;
+    stt.rel_grad_inf = g0inf > 0 ? last_ginf / g0inf : 0.0;
+    stt.converged = stt.rel_grad_inf <= o.rel_tol ? 1 : 0;
+  }
+};
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+
+namespace {
+
+bool good_len(int n) {
+  if (n < 4 || n > 1024) return false;
+  FftPlan p;
+  return make_plan(n, &p);
+}
+
+template <typename F> ga_status guard(ga_ctx* c, F&& f) {
+  try {
+    f();
+    return GA_OK;
+  } catch (const Fail& e) {
+    return e.st;
+  } catch (...) {
+    set_err(c, "unexpected host exception");
+    return GA_ERR_CUDA;
+  }
+}
+
+
+// Run fn(engine) with the engine of the context's precision.
+template <typename F> ga_status dispatch(ga_ctx* c, F&& fn) {
+  if (!c) return GA_ERR_ARG;
+  return guard(c, [&] {
+    if (c->ef) fn(*c->ef);
+    else fn(*c->ed);
+  });
+}
+
+// Copy a caller buffer of `count` elements into device staging (or use it directly).
+template <typename T> const T* stage_in(Engine<T>& e, const void* p, long long count, int mem, T* staging) {
+  if (mem == GA_MEM_DEVICE) return static_cast<const T*>(p);
+  e.ck(cudaMemcpyAsync(staging, p, sizeof(T) * count, cudaMemcpyHostToDevice, e.st), "H2D copy");
+  return staging;
+}
+template <typename T> void stage_out(Engine<T>& e, void* p, const T* src, long long count, int mem) {
+  if (mem == GA_MEM_DEVICE) {
+    if (p != static_cast<const void*>(src)) e.ck(cudaMemcpyAsync(p, src, sizeof(T) * count, cudaMemcpyDeviceToDevice, e.st), "D2D copy");
+  } else {
+    e.ck(cudaMemcpyAsync(p, src, sizeof(T) * count, cudaMemcpyDeviceToHost, e.st), "D2H copy");
+  }
+  e.ck(cudaStreamSynchronize(e.st), "sync");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ga_status_str(ga_status s) {
+  switch (s) {
+    case GA_OK: return "GA_OK";
+    case GA_ERR_ARG: return "GA_ERR_ARG";
+    case GA_ERR_CUDA: return "GA_ERR_CUDA";
+    case GA_ERR_NOMEM: return "GA_ERR_NOMEM";
+    case GA_ERR_NAN: return "GA_ERR_NAN";
+    case GA_ERR_LINESEARCH: return "GA_ERR_LINESEARCH";
+    case GA_ERR_NOT_CONVERGED: return "GA_ERR_NOT_CONVERGED";
+    case GA_ERR_TIMEOUT: return "GA_ERR_TIMEOUT";
+  }
+  return "GA_ERR_UNKNOWN";
+}
+
+static thread_local std::string g_setup_err;
+
+const char* ga_last_error(const ga_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_setup_err.empty() ? "null context" : g_setup_err.c_str();
+}
+
+ga_status ga_setup(const ga_problem_desc* desc, const ga_solver_opts* opts, const void* m0, const void* m1,
+                   int mem, void* stream, ga_ctx** out) {
+  if (!out) return GA_ERR_ARG;
+  *out = nullptr;
+  if (!desc || !opts || !m0 || !m1) return GA_ERR_ARG;
+  const ga_problem_desc& d = *desc;
+  const ga_solver_opts& o = *opts;
+  bool ok = (d.dim == 2 || d.dim == 3) && d.nt >= 1 && d.nt <= 4096 && d.model >= 0 && d.model <= 2 &&
+            d.reg_order >= 1 && d.reg_order <= 3 && d.alpha > 0.0 && std::isfinite(d.alpha) &&
+            (d.prec == GA_PREC_FP64 || d.prec == GA_PREC_MIXED) && d.ckpt_every >= 0 &&
+            (mem == GA_MEM_HOST || mem == GA_MEM_DEVICE);
+  for (int a = 0; ok && a < d.dim; ++a) ok = good_len(d.n[a]);
+  ok = ok && o.window >= 0 && o.window < kMaxWin && o.window + 2 <= kMaxDots && o.sigma >= 1 && o.tau >= 0 &&
+       o.max_iter >= 1 && o.rel_tol >= 0.0 && o.armijo_c > 0.0 && o.max_backtracks >= 0 &&
+       o.max_backtracks <= 200 && (o.variant == 1 || o.variant == 2) &&
+       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD);
+  if (!ok) {
+    g_setup_err = "invalid problem descriptor or solver options";
+    return GA_ERR_ARG;
+  }
+  ga_ctx* c = new ga_ctx();
+  c->desc = d;
+  c->opts = o;
+  c->st = static_cast<cudaStream_t>(stream);
+  c->prec = d.prec;
+  c->stats = ga_stats{};
+  c->stats.rho_mem = 1.0;
+  ga_status s = guard(c, [&] {
+    if (d.prec == GA_PREC_MIXED) {
+      c->ef = new Engine<float>();
+      c->ef->init(c, m0, m1, mem);
+    } else {
+      c->ed = new Engine<double>();
+      c->ed->init(c, m0, m1, mem);
+    }
+  });
+  if (s != GA_OK) {
+    g_setup_err = c->err;
+    delete c->ef;
+    delete c->ed;
+    delete c;
+    return s;
+  }
+  *out = c;
+  return GA_OK;
+}
+
+void ga_destroy(ga_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  delete ctx->ef;
+  delete ctx->ed;
+  delete ctx;
+}
+
+ga_status ga_objective(ga_ctx* ctx, const void* v, int mem, double* obj) {
+  if (!ctx || !v || !obj || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    auto* vin = stage_in(e, v, e.vl, mem, e.io_a);
+    const double J = e.objective(vin);
+    if (!std::isfinite(J)) {
+      set_err(ctx, "non-finite objective");
+      throw Fail{GA_ERR_NAN};
+    }
+    *obj = J;
+  });
+}
+
+ga_status ga_gradient(ga_ctx* ctx, const void* v, void* g, int mem, double* obj) {
+  if (!ctx || !v || !g || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    auto* vin = stage_in(e, v, e.vl, mem, e.io_a);
+    T* gout = mem == GA_MEM_DEVICE ? static_cast<T*>(g) : e.io_b;
+    const double J = e.gradient(vin, gout, nullptr);
+    if (obj) *obj = J;
+    stage_out(e, g, gout, e.vl, mem);
+  });
+}
+
+ga_status ga_precond(ga_ctx* ctx, const void* g, void* s, int mem) {
+  if (!ctx || !g || !s || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    auto* gin = stage_in(e, g, e.vl, mem, e.io_a);
+    T* sout = mem == GA_MEM_DEVICE ? static_cast<T*>(s) : e.io_b;
+    e.precond(gin, sout);
+    stage_out(e, s, sout, e.vl, mem);
+  });
+}
+
+ga_status ga_reset(ga_ctx* ctx) {
+  if (!ctx) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) { e.reset(); });
+}
+
+ga_status ga_get_stats(const ga_ctx* ctx, ga_stats* stats) {
+  if (!ctx || !stats) return GA_ERR_ARG;
+  *stats = ctx->stats;
+  return GA_OK;
+}
+
+ga_status ga_step(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
+  if (!ctx || !v_inout || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  ga_status s = dispatch(ctx, [&](auto& e) {
+    if (!e.started) {
+      auto* vin = stage_in(e, v_inout, e.vl, mem, e.io_a);
+      e.start(vin);
+    }
+    e.step();
+    stage_out(e, v_inout, e.win.front().first, e.vl, mem);
+  });
+  ctx->stats.t_total_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = ctx->stats;
+  return s;
+}
+
+ga_status ga_solve(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
+  if (!ctx || !v_inout || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  ga_status s = dispatch(ctx, [&](auto& e) {
+    auto* vin = stage_in(e, v_inout, e.vl, mem, e.io_a);
+    e.start(vin);
+    if (ctx->stats.rel_grad_inf > ctx->opts.rel_tol) {
+      while (e.k < ctx->opts.max_iter) {
+        e.step();
+        if (ctx->stats.converged) break;
+      }
+    } else {
+      ctx->stats.converged = 1;
+    }
+    stage_out(e, v_inout, e.win.front().first, e.vl, mem);
+  });
+  ctx->stats.t_total_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = ctx->stats;
+  if (s == GA_OK && !ctx->stats.converged) return GA_ERR_NOT_CONVERGED;
+  return s;
+}
+
+ga_status ga_solve_batch(int count, ga_ctx* const* ctxs, void* const* v, int mem, ga_stats* stats) {
+  if (count < 0 || (count > 0 && (!ctxs || !v))) return GA_ERR_ARG;
+  ga_status worst = GA_OK;
+  for (int i = 0; i < count; ++i) {
+    ga_status s = ga_solve(ctxs[i], v[i], mem, stats ? &stats[i] : nullptr);
+    if (s == GA_ERR_NOT_CONVERGED) {
+      if (worst == GA_OK) worst = s;
+    } else if (s != GA_OK) {
+      return s;
+    }
+  }
+  return worst;
+}
+
+// ---- operator-level entry points (ga_ops.h) --------------------------------------------------------
+
+ga_status ga_op_departure(ga_ctx* ctx, const void* v, void* xm, void* xp) {
+  if (!ctx || !v || !xm || !xp) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    e.ck(launch_departure<T>(e.g, static_cast<const T*>(v), static_cast<T*>(xm), static_cast<T*>(xp), (T)e.ht,
+                             e.st), "departure");
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_forward(ga_ctx* ctx, const void* v, void* states) {
+  if (!ctx || !v || !states) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    const T* vv = static_cast<const T*>(v);
+    T* out = static_cast<T*>(states);
+    e.compute_mu(vv);
+    e.ck(launch_departure<T>(e.g, vv, e.xm, e.xp, (T)e.ht, e.st), "departure");
+    e.ck(cudaMemcpyAsync(out, e.m0, sizeof(T) * e.nv, cudaMemcpyDeviceToDevice, e.st), "copy");
+    for (int j = 0; j < e.nt; ++j) e.sl_forward(out + (long long)j * e.nv, out + (long long)(j + 1) * e.nv);
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_adjoint(ga_ctx* ctx, const void* v, const void* lam1, void* lams) {
+  if (!ctx || !v || !lam1 || !lams) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    const T* vv = static_cast<const T*>(v);
+    T* out = static_cast<T*>(lams);
+    e.compute_mu(vv);
+    e.ck(launch_departure<T>(e.g, vv, e.xm, e.xp, (T)e.ht, e.st), "departure");
+    const long long nv = e.nv;
+    e.ck(cudaMemcpyAsync(out + (long long)e.nt * nv, lam1, sizeof(T) * nv, cudaMemcpyDeviceToDevice, e.st), "copy");
+    for (int j = e.nt - 1; j >= 0; --j) e.sl_adjoint(out + (long long)(j + 1) * nv, out + (long long)j * nv);
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_body_force(ga_ctx* ctx, const void* v, const void* lam1, void* b) {
+  if (!ctx || !v || !lam1 || !b) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    const T* vv = static_cast<const T*>(v);
+    e.compute_mu(vv);
+    e.ck(launch_departure<T>(e.g, vv, e.xm, e.xp, (T)e.ht, e.st), "departure");
+    e.forward_all();
+    e.ck(cudaMemcpyAsync(e.lam[0], lam1, sizeof(T) * e.nv, cudaMemcpyDeviceToDevice, e.st), "copy");
+    e.body_force(e.lam[0]);
+    e.ck(cudaMemcpyAsync(b, e.body, sizeof(T) * e.vl, cudaMemcpyDeviceToDevice, e.st), "copy");
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_deriv(ga_ctx* ctx, const void* f, int axis, void* df) {
+  if (!ctx || !f || !df || f == df) return GA_ERR_ARG;
+  if (axis < 0 || axis >= ctx->desc.dim) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    e.deriv(e.g.axis_of(axis), static_cast<const T*>(f), nullptr, static_cast<T*>(df), 1.0, false);
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_div(ga_ctx* ctx, const void* v, void* mu) {
+  if (!ctx || !v || !mu) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    e.compute_mu(static_cast<const T*>(v));
+    e.ck(cudaMemcpyAsync(mu, e.mu, sizeof(T) * e.nv, cudaMemcpyDeviceToDevice, e.st), "copy");
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_fft_r2c(ga_ctx* ctx, const void* f, void* fhat) {
+  if (!ctx || !f || !fhat) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    e.r2c(static_cast<const T*>(f), static_cast<cx<T>*>(fhat));
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_fft_c2r(ga_ctx* ctx, const void* fhat, void* f) {
+  if (!ctx || !fhat || !f) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    e.ck(cudaMemcpyAsync(e.bh, fhat, sizeof(cx<T>) * e.g.nhalf, cudaMemcpyDeviceToDevice, e.st), "copy");
+    e.c2r(e.bh, static_cast<T*>(f));
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_apply_L(ga_ctx* ctx, const void* v, void* Lv) {
+  if (!ctx || !v || !Lv) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    const T* vv = static_cast<const T*>(v);
+    for (int c = 0; c < e.dim; ++c) e.r2c(vv + c * e.nv, e.bh + c * e.g.nhalf);
+    SpecArgs sa{SPEC_APPLY_L, e.s, e.alpha, 0, 0};
+    e.ck(launch_spectral<T>(e.g, sa, e.bh, nullptr, e.st), "spectral");
+    for (int c = 0; c < e.dim; ++c) e.c2r(e.bh + c * e.g.nhalf, static_cast<T*>(Lv) + c * e.nv);
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_leray(ga_ctx* ctx, const void* v, void* pv) {
+  if (!ctx || !v || !pv) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    const T* vv = static_cast<const T*>(v);
+    for (int c = 0; c < e.dim; ++c) e.r2c(vv + c * e.nv, e.bh + c * e.g.nhalf);
+    SpecArgs sa{SPEC_LERAY, e.s, e.alpha, 1, 0};
+    e.ck(launch_spectral<T>(e.g, sa, e.bh, nullptr, e.st), "spectral");
+    for (int c = 0; c < e.dim; ++c) e.c2r(e.bh + c * e.g.nhalf, static_cast<T*>(pv) + c * e.nv);
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_op_dots(ga_ctx* ctx, const void* a, const void* const* b, int count, size_t len, double* out) {
+  if (!ctx || !a || !b || !out || count < 1 || count > kMaxDots || len < 1) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    std::vector<const T*> bl(count);
+    for (int i = 0; i < count; ++i) bl[i] = static_cast<const T*>(b[i]);
+    e.ck(launch_dots<T>(static_cast<const T*>(a), bl.data(), count, (long long)len, e.dpart, e.dres + 16, e.st),
+         "dots");
+    e.read_results(16 + count);
+    for (int i = 0; i < count; ++i) out[i] = e.hres[16 + i];
+  });
+}
+
+ga_status ga_op_lsq(ga_ctx* ctx, int m, double c, const double* a, const double* M, double* beta) {
+  if (!ctx || !a || !M || !beta || m < 1 || m > kMaxWin) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    std::vector<double> h(1 + m + m * m + m);
+    h[0] = c;
+    for (int i = 0; i < m; ++i) h[1 + i] = a[i];
+    double* dd = e.dpart;  // scratch: dots at 0, M at 1 + m, beta after
+    e.ck(cudaMemcpyAsync(dd, h.data(), sizeof(double) * (1 + m), cudaMemcpyHostToDevice, e.st), "copy");
+    e.ck(cudaMemcpyAsync(dd + 1 + m, M, sizeof(double) * m * m, cudaMemcpyHostToDevice, e.st), "copy");
+    e.ck(launch_lsq(m, dd, dd + 1 + m, m, dd + 1 + m + m * m, nullptr, e.st), "lsq");
+    e.ck(cudaMemcpyAsync(beta, dd + 1 + m + m * m, sizeof(double) * m, cudaMemcpyDeviceToHost, e.st), "copy");
+    e.ck(cudaStreamSynchronize(e.st), "sync");
+  });
+}
+
+ga_status ga_transport(ga_ctx* ctx, const void* v, void* m1_out, int mem) {
+  if (!ctx || !v || !m1_out || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    auto* vin = stage_in(e, v, e.vl, mem, e.io_a);
+    if (e.needs_mu_forward()) e.compute_mu(vin);
+    const auto* mT = e.forward_final(vin);
+    stage_out(e, m1_out, mT, e.nv, mem);
+  });
+}
+
+ga_status ga_transport_vjp(ga_ctx* ctx, const void* v, const void* gamma, void* grad_v, int mem) {
+  if (!ctx || !v || !gamma || !grad_v || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    auto* vin = stage_in(e, v, e.vl, mem, e.io_a);
+    const T* gam = stage_in(e, gamma, e.nv, mem, e.lam[0]);
+    if (gam != e.lam[0])
+      e.ck(cudaMemcpyAsync(e.lam[0], gam, sizeof(T) * e.nv, cudaMemcpyDeviceToDevice, e.st), "copy");
+    e.compute_mu(vin);
+    e.ck(launch_departure<T>(e.g, vin, e.xm, e.xp, (T)e.ht, e.st), "departure");
+    e.forward_all();
+    e.body_force(e.lam[0]);
+    // grad_v = -b
+    e.ck(launch_axpy<T>(e.io_b, e.body, e.body, -2.0, e.vl, e.st), "negate");
+    stage_out(e, grad_v, e.io_b, e.vl, mem);
+  });
+}
+
+// ---- event timing of one kernel class over a region (used by the benchmark) --------------------------
+ga_status ga_prof_start(ga_ctx* ctx, int kernel_class) {
+  if (!ctx || kernel_class < 0 || kernel_class > 2) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    if (e.prof_ev.empty()) {
+      e.prof_ev.resize(4096);
+      for (auto& ev : e.prof_ev) e.ck(cudaEventCreate(&ev), "cudaEventCreate");
+    }
+    e.prof_class = kernel_class;
+    e.prof_used = 0;
+    e.prof_ms = 0.0;
+    e.prof_launches = 0;
+  });
+}
+
+ga_status ga_prof_stop(ga_ctx* ctx, double* total_ms, long long* launches) {
+  if (!ctx || !total_ms || !launches) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    e.prof_flush();
+    *total_ms = e.prof_ms;
+    *launches = e.prof_launches;
+    e.prof_class = -1;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal launchers of the GB300 GA-NGMRES library. Every launcher enqueues work on `st`
+// and returns cudaGetLastError() of its launch(es).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ga {
+
+constexpr int kThreads = 256;       // threads per CTA of the streaming kernels
+constexpr int kRedBlocks = 152 * 4; // CTAs of the reduction kernels (4 per SM of a GB300)
+constexpr int kMaxDots = 32;        // vectors per multi-dot call
+constexpr int kMaxWin = 31;         // window entries in the least-squares kernel
+
+template <typename T> struct PtrList { const T* p[16]; };
+
+template <typename T> struct FftTables {
+  FftPlan plan[3];
+  const cx<T>* tw[3];  // device tables exp(-2 pi i m / n_a), m < n_a
+};
+
+// ---- spectral / FFT passes (fft_kernels.cu) --------------------------------------------------
+// out (+)= coef * mult * d f / d x_axis (1D spectral derivative along internal axis `axis`).
+template <typename T>
+cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult,
+                         T* out, T coef, bool accumulate, cudaStream_t st);
+// Forward real-to-complex 3D (or 2D) FFT, unnormalised; fh: nhalf complex.
+template <typename T>
+cudaError_t launch_r2c(const Grid& g, const FftTables<T>& ft, const T* f, cx<T>* fh, cudaStream_t st);
+// Inverse (normalised by 1/nvox); overwrites fh.
+template <typename T>
+cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, cudaStream_t st);
+
+// ---- pointwise spectral operators (spectral_kernels.cu) --------------------------------------
+enum SpecMode { SPEC_APPLY_L = 0, SPEC_LERAY = 1, SPEC_PRECOND = 2, SPEC_EPILOGUE = 3 };
+struct SpecArgs {
+  int mode;
+  int s;            // regulariser order
+  double alpha;
+  int project;      // apply the Leray projector (incompressible model)
+  int want_s;       // EPILOGUE: also write the preconditioned direction into `v`
+};
+// Fields: x[c] (dim half spectra) updated in place; EPILOGUE: x = b^ in, g^ out; v = v^ in,
+// s^ out (when want_s).
+template <typename T>
+cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cx<T>* v, cudaStream_t st);
+// partial[b] = sum over the half spectrum (weights 1/2) of |k|^{2s} |v^_c|^2 summed over c.
+template <typename T>
+cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partial, cudaStream_t st);
+
+// ---- semi-Lagrangian transport (sl_kernels.cu) -----------------------------------------------
+// Displacements (grid units) of the RK2 departure points X- (xm) and X+ (xp).
+template <typename T>
+cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cudaStream_t st);
+// One state step m_{j+1} = I[m_j](X-) (continuity: with the RK2 source of -pi div v).
+template <typename T>
+cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T* xm, const T* mu,
+                              T* out, T ht, cudaStream_t st);
+// One adjoint step lambda_j from lambda_{j+1} (advection: with the source lambda div v).
+template <typename T>
+cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const T* xp, const T* mu,
+                              T* out, T ht, cudaStream_t st);
+
+// ---- reductions and vector kernels (reduce_kernels.cu) ---------------------------------------
+// out[i] = sum_j a[j] b_i[j] for i < count (count <= 32), FP64 compensated; out is device memory.
+template <typename T>
+cudaError_t launch_dots(const T* a, const T* const* b, int count, long long len, double* partial,
+                        double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_maxabs(const T* x, long long len, double* partial, double* out, cudaStream_t st);
+// lam = m1 - mT and out[0] = sum (mT - m1)^2.
+template <typename T>
+cudaError_t launch_mismatch(const T* mT, const T* m1, T* lam, long long len, double* partial,
+                            double* out, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partial, int count, int nblocks, double* out, cudaStream_t st);
+// y = x + a s
+template <typename T>
+cudaError_t launch_axpy(T* y, const T* x, const T* s, double a, long long len, cudaStream_t st);
+// out = q + sum_i beta_i (q - v_i), beta on the device
+template <typename T>
+cudaError_t launch_combine(T* out, const T* q, const T* const* v, const double* beta, int m, long long len,
+                           cudaStream_t st);
+// NGMRES least squares from FP64 Gram data on the device (single CTA):
+// dots[0] = c, dots[1 + i] = a_i, M (m x m, leading dim ldm) -> beta[0..m)
+cudaError_t launch_lsq(int m, const double* dots, const double* M, int ldm, double* beta, double* info,
+                       cudaStream_t st);
+// Window Gram update: M' = [[row0, row[1..]], [row[1..]^T, M[:mkeep, :mkeep]]]
+cudaError_t launch_gram_push(double* M, int ldm, int mkeep, const double* row, cudaStream_t st);
+
+}  // namespace ga

@@ -1,0 +1,369 @@
+// Reductions and small vector kernels of the solver (Sec. 2.3; Alg. 1-3).
+//
+// Inner products are FP64-accurate and deterministic: every thread accumulates a compensated
+// partial sum (FP32 data: a double-float pair, products split exactly with an FMA; FP64 data:
+// Neumaier summation), CTAs combine their threads in FP64 in a fixed tree order and write one
+// partial per CTA; a single-CTA pass sums the partials in a fixed order. The grid size is fixed,
+// so results do not depend on scheduling.
+//
+// The NGMRES least squares (Alg. 1, "arg min") is solved from its Gram data in one CTA: the normal
+// matrix G_ij = <g_q - g_i, g_q - g_j> = c - a_i - a_j + M_ij and right-hand side -(c - a_i)
+// are diagonalised by cyclic Jacobi rotations in FP64 and eigenvalues below 1e-14 max are dropped.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace ga {
+
+namespace {
+
+struct AccF {  // double-float accumulator for FP32 products
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+struct AccD {  // Neumaier accumulator for FP64 products
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) {
+    const double p = a * b;
+    const double t = s + p;
+    c += (fabs(s) >= fabs(p)) ? (s - t) + p : (p - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = AccF; };
+template <> struct AccOf<double> { using type = AccD; };
+
+// Sum x over the CTA (fixed order); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double red[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+  }
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double x) {
+  __shared__ double red[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, off));
+  }
+  return r;
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads)
+k_dots(const T* __restrict__ a, PtrList<T> b, int count, long long len, double* __restrict__ partial) {
+  using Acc = typename AccOf<T>::type;
+  Acc acc[NB];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T av = a[i];
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (k < count) acc[k].add_prod(av, b.p[k][i]);
+  }
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if (k < count) {
+      const double s = block_sum(acc[k].value());
+      if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_maxabs(const T* __restrict__ x, long long len, double* __restrict__ partial) {
+  double m = 0.0;
+  int bad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = fabs((double)x[i]);
+    if (!(v <= 1.0e300)) bad = 1;  // NaN or Inf
+    m = fmax(m, v);
+  }
+  if (bad) m = __longlong_as_double(0x7ff8000000000000LL);  // propagate NaN
+  // fmax drops NaN, so carry it explicitly through the block maximum
+  const int anybad = __syncthreads_or(bad);
+  const double r = block_max(bad ? 0.0 : m);
+  if (threadIdx.x == 0) partial[blockIdx.x] = anybad ? __longlong_as_double(0x7ff8000000000000LL) : r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_mismatch(const T* __restrict__ mT, const T* __restrict__ m1, T* __restrict__ lam, long long len,
+           double* __restrict__ partial) {
+  using Acc = typename AccOf<T>::type;
+  Acc acc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T r = m1[i] - mT[i];
+    if (lam) lam[i] = r;
+    acc.add_prod(r, r);
+  }
+  const double s = block_sum(acc.value());
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out[k] = sum_b partial[k * nblocks + b] in a fixed order (Neumaier), k < count.
+__global__ void k_sum_partials(const double* __restrict__ partial, int count, int nblocks,
+                               double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= count) return;
+  double s = 0.0, c = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    const double p = partial[(long long)k * nblocks + b];
+    const double t = s + p;
+    c += (fabs(s) >= fabs(p)) ? (s - t) + p : (p - t) + s;
+    s = t;
+  }
+  out[k] = s + c;
+}
+
+__global__ void k_max_partials(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+  double m = 0.0;
+  int bad = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const double p = partial[b];
+    if (!(p <= 1.0e300)) bad = 1;
+    else m = fmax(m, p);
+  }
+  const int anybad = __syncthreads_or(bad);
+  const double r = block_max(m);
+  if (threadIdx.x == 0) out[0] = anybad ? __longlong_as_double(0x7ff8000000000000LL) : r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_axpy(T* __restrict__ y, const T* __restrict__ x, const T* __restrict__ s, T a, long long len) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] + a * s[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_combine(T* __restrict__ out, const T* __restrict__ q, PtrList<T> v, const double* __restrict__ beta,
+          int m, int accumulate, long long len) {
+  T bt[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) bt[k] = k < m ? (T)beta[k] : T(0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T qi = q[i];
+    T acc = accumulate ? out[i] : qi;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < m) acc += bt[k] * (qi - v.p[k][i]);
+    out[i] = acc;
+  }
+}
+
+// Cyclic Jacobi eigen-solve of the m x m normal equations, one thread (m <= kMaxWin).
+__global__ void k_lsq(int m, const double* __restrict__ dots, const double* __restrict__ M, int ldm,
+                      double* __restrict__ beta, double* __restrict__ info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double G[kMaxWin * kMaxWin];
+  double U[kMaxWin * kMaxWin];
+  double r[kMaxWin];
+  const double c = dots[0];
+  for (int i = 0; i < m; ++i) {
+    r[i] = c - dots[1 + i];
+    for (int j = 0; j < m; ++j) {
+      G[i * m + j] = c - dots[1 + i] - dots[1 + j] + M[i * ldm + j];
+      U[i * m + j] = (i == j) ? 1.0 : 0.0;
+    }
+  }
+  for (int i = 0; i < m; ++i)  // symmetrise against rounding of the expansion
+    for (int j = i + 1; j < m; ++j) {
+      const double s = 0.5 * (G[i * m + j] + G[j * m + i]);
+      G[i * m + j] = s;
+      G[j * m + i] = s;
+    }
+  double fro = 0.0;
+  for (int i = 0; i < m * m; ++i) fro += G[i] * G[i];
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j) off += 2.0 * G[i * m + j] * G[i * m + j];
+    if (off <= 1e-30 * fro || off == 0.0) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = G[p * m + q];
+        if (apq == 0.0) continue;
+        const double app = G[p * m + p], aqq = G[q * m + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < m; ++k) {  // G <- J^T G J
+          const double gkp = G[k * m + p], gkq = G[k * m + q];
+          G[k * m + p] = cs * gkp - sn * gkq;
+          G[k * m + q] = sn * gkp + cs * gkq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double gpk = G[p * m + k], gqk = G[q * m + k];
+          G[p * m + k] = cs * gpk - sn * gqk;
+          G[q * m + k] = sn * gpk + cs * gqk;
+        }
+        for (int k = 0; k < m; ++k) {  // U <- U J
+          const double ukp = U[k * m + p], ukq = U[k * m + q];
+          U[k * m + p] = cs * ukp - sn * ukq;
+          U[k * m + q] = sn * ukp + cs * ukq;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int i = 0; i < m; ++i) lmax = fmax(lmax, G[i * m + i]);
+  const double thr = 1e-14 * lmax;
+  for (int i = 0; i < m; ++i) beta[i] = 0.0;
+  int rank = 0;
+  for (int k = 0; k < m; ++k) {
+    const double lam = G[k * m + k];
+    if (!(lam > thr)) continue;
+    ++rank;
+    double proj = 0.0;
+    for (int i = 0; i < m; ++i) proj += U[i * m + k] * r[i];
+    const double coef = -proj / lam;
+    for (int i = 0; i < m; ++i) beta[i] += coef * U[i * m + k];
+  }
+  if (info) {
+    info[0] = (double)rank;
+    info[1] = (double)sweep;
+    info[2] = lmax;
+  }
+}
+
+__global__ void k_gram_push(double* __restrict__ M, int ldm, int mkeep, const double* __restrict__ row) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // shift the kept block down-right by one, in place from the bottom-right corner
+  for (int i = mkeep - 1; i >= 0; --i)
+    for (int j = mkeep - 1; j >= 0; --j) M[(i + 1) * ldm + (j + 1)] = M[i * ldm + j];
+  M[0] = row[0];
+  for (int i = 0; i < mkeep; ++i) {
+    M[(i + 1) * ldm] = row[1 + i];
+    M[i + 1] = row[1 + i];
+  }
+}
+
+inline unsigned grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  const long long cap = 152LL * 8;
+  return (unsigned)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dots(const T* a, const T* const* b, int count, long long len, double* partial, double* out,
+                        cudaStream_t st) {
+  if (count < 1 || count > kMaxDots) return cudaErrorInvalidValue;
+  for (int base = 0; base < count; base += 16) {
+    PtrList<T> pl;
+    const int cnt = (count - base) < 16 ? (count - base) : 16;
+    for (int k = 0; k < 16; ++k) pl.p[k] = k < cnt ? b[base + k] : nullptr;
+    if (cnt <= 4)
+      k_dots<T, 4><<<kRedBlocks, kThreads, 0, st>>>(a, pl, cnt, len, partial + (long long)base * kRedBlocks);
+    else if (cnt <= 8)
+      k_dots<T, 8><<<kRedBlocks, kThreads, 0, st>>>(a, pl, cnt, len, partial + (long long)base * kRedBlocks);
+    else
+      k_dots<T, 16><<<kRedBlocks, kThreads, 0, st>>>(a, pl, cnt, len, partial + (long long)base * kRedBlocks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_sum_partials<<<1, 32, 0, st>>>(partial, count, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_maxabs(const T* x, long long len, double* partial, double* out, cudaStream_t st) {
+  k_maxabs<T><<<kRedBlocks, kThreads, 0, st>>>(x, len, partial);
+  k_max_partials<<<1, kThreads, 0, st>>>(partial, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mismatch(const T* mT, const T* m1, T* lam, long long len, double* partial, double* out,
+                            cudaStream_t st) {
+  k_mismatch<T><<<kRedBlocks, kThreads, 0, st>>>(mT, m1, lam, len, partial);
+  k_sum_partials<<<1, 32, 0, st>>>(partial, 1, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* partial, int count, int nblocks, double* out, cudaStream_t st) {
+  k_sum_partials<<<1, 32, 0, st>>>(partial, count, nblocks, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_axpy(T* y, const T* x, const T* s, double a, long long len, cudaStream_t st) {
+  k_axpy<T><<<grid_for(len), kThreads, 0, st>>>(y, x, s, (T)a, len);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_combine(T* out, const T* q, const T* const* v, const double* beta, int m, long long len,
+                           cudaStream_t st) {
+  if (m < 1) return cudaMemcpyAsync(out, q, sizeof(T) * len, cudaMemcpyDeviceToDevice, st);
+  for (int base = 0; base < m; base += 16) {
+    PtrList<T> pl;
+    const int cnt = (m - base) < 16 ? (m - base) : 16;
+    for (int k = 0; k < 16; ++k) pl.p[k] = k < cnt ? v[base + k] : nullptr;
+    k_combine<T><<<grid_for(len), kThreads, 0, st>>>(out, q, pl, beta + base, cnt, base > 0 ? 1 : 0, len);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_lsq(int m, const double* dots, const double* M, int ldm, double* beta, double* info,
+                       cudaStream_t st) {
+  if (m < 1 || m > kMaxWin) return cudaErrorInvalidValue;
+  k_lsq<<<1, 32, 0, st>>>(m, dots, M, ldm, beta, info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_push(double* M, int ldm, int mkeep, const double* row, cudaStream_t st) {
+  k_gram_push<<<1, 32, 0, st>>>(M, ldm, mkeep, row);
+  return cudaGetLastError();
+}
+
+#define GA_INST(T)                                                                                   \
+  template cudaError_t launch_dots<T>(const T*, const T* const*, int, long long, double*, double*,    \
+                                      cudaStream_t);                                                  \
+  template cudaError_t launch_maxabs<T>(const T*, long long, double*, double*, cudaStream_t);         \
+  template cudaError_t launch_mismatch<T>(const T*, const T*, T*, long long, double*, double*,        \
+                                          cudaStream_t);                                              \
+  template cudaError_t launch_axpy<T>(T*, const T*, const T*, double, long long, cudaStream_t);       \
+  template cudaError_t launch_combine<T>(T*, const T*, const T* const*, const double*, int, long long, \
+                                         cudaStream_t);
+GA_INST(float)
+GA_INST(double)
+#undef GA_INST
+
+}  // namespace ga

@@ -1,0 +1,160 @@
+// Pointwise operators on the half spectrum (Sec. 2.2 diagonal scalings; Sec. 3.6 Leray projector).
+//
+// Half-spectrum entry (i0, i1, i2) has wavenumbers k_a = i_a for i_a <= n_a/2, else i_a - n_a
+// (axis 2 stores only i2 <= n2/2). Even symbols use the full k (Nyquist included):
+// L^ = |k|^{2s}. Derivative symbols use k~ (zero at the Nyquist index). The inverse (alpha L)^{-1}
+// sets zero entries of L^ to one.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace ga {
+
+namespace {
+
+template <typename R> struct KVec {
+  R k[3];   // full wavenumbers (even symbols)
+  R kt[3];  // derivative wavenumbers
+};
+
+template <typename R> __device__ __forceinline__ KVec<R> kvec_of(const Grid& g, long long idx) {
+  const int i2 = (int)(idx % g.n2h);
+  const long long r = idx / g.n2h;
+  const int i1 = (int)(r % g.n[1]);
+  const int i0 = (int)(r / g.n[1]);
+  const int ii[3] = {i0, i1, i2};
+  KVec<R> kv;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int n = g.n[a];
+    const int i = ii[a];
+    const int k = (2 * i <= n) ? i : i - n;
+    kv.k[a] = (R)k;
+    kv.kt[a] = (2 * i == n) ? R(0) : (R)k;
+  }
+  return kv;
+}
+
+template <typename R> __device__ __forceinline__ R symbol_L(const KVec<R>& kv, int s) {
+  const R k2 = kv.k[0] * kv.k[0] + kv.k[1] * kv.k[1] + kv.k[2] * kv.k[2];
+  R r = k2;
+  for (int i = 1; i < s; ++i) r *= k2;
+  return r;
+}
+
+// Leray projection of the dim-component vector x (component c along axis 3 - dim + c).
+template <typename T>
+__device__ __forceinline__ void leray(const KVec<T>& kv, int dim, cx<T>* x) {
+  T kc[3];
+  T k2 = T(0);
+  for (int c = 0; c < dim; ++c) {
+    kc[c] = kv.kt[3 - dim + c];
+    k2 += kc[c] * kc[c];
+  }
+  if (k2 == T(0)) return;
+  T dr = T(0), di = T(0);
+  for (int c = 0; c < dim; ++c) {
+    dr += kc[c] * x[c].x;
+    di += kc[c] * x[c].y;
+  }
+  dr /= k2;
+  di /= k2;
+  for (int c = 0; c < dim; ++c) {
+    x[c].x -= kc[c] * dr;
+    x[c].y -= kc[c] * di;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_spectral(Grid g, SpecArgs a, cx<T>* __restrict__ x, cx<T>* __restrict__ v) {
+  const long long nh = g.nhalf;
+  const int dim = g.dim;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nh;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const KVec<T> kv = kvec_of<T>(g, idx);
+    const T L = symbol_L<T>(kv, a.s);
+    cx<T> xv[3];
+    for (int c = 0; c < dim; ++c) xv[c] = x[c * nh + idx];
+    if (a.mode == SPEC_APPLY_L) {
+      for (int c = 0; c < dim; ++c) x[c * nh + idx] = cscale(xv[c], (T)L);
+      continue;
+    }
+    if (a.mode == SPEC_LERAY) {
+      leray<T>(kv, dim, xv);
+      for (int c = 0; c < dim; ++c) x[c * nh + idx] = xv[c];
+      continue;
+    }
+    const T inv = T(-1) / ((T)a.alpha * (L == T(0) ? T(1) : L));
+    if (a.mode == SPEC_PRECOND) {
+      if (a.project) leray<T>(kv, dim, xv);
+      for (int c = 0; c < dim; ++c) x[c * nh + idx] = cscale(xv[c], (T)inv);
+      continue;
+    }
+    // SPEC_EPILOGUE: g^ = alpha L^ v^ + (P) b^ ; optionally s^ = -(P g^) / (alpha L^_fix)
+    if (a.project) leray<T>(kv, dim, xv);
+    cx<T> gv[3];
+    const T aL = (T)(a.alpha * L);
+    for (int c = 0; c < dim; ++c) {
+      const cx<T> vv = v[c * nh + idx];
+      gv[c] = mk<T>(aL * vv.x + xv[c].x, aL * vv.y + xv[c].y);
+      x[c * nh + idx] = gv[c];
+    }
+    if (a.want_s) {
+      if (a.project) leray<T>(kv, dim, gv);
+      for (int c = 0; c < dim; ++c) v[c * nh + idx] = cscale(gv[c], (T)inv);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_reg_sum(Grid g, int s, const cx<T>* __restrict__ vh, double* __restrict__ partial) {
+  const long long nh = g.nhalf;
+  double acc = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nh;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const KVec<double> kv = kvec_of<double>(g, idx);
+    const int i2 = (int)(idx % g.n2h);
+    const double w = (i2 == 0 || 2 * i2 == g.n[2]) ? 1.0 : 2.0;
+    const double L = symbol_L<double>(kv, s);
+    double e = 0.0;
+    for (int c = 0; c < g.dim; ++c) {
+      const cx<T> z = vh[c * nh + idx];
+      e += (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+    }
+    acc += w * L * e;
+  }
+  __shared__ double red[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double r = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cx<T>* v, cudaStream_t st) {
+  long long blocks = (g.nhalf + kThreads - 1) / kThreads;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_spectral<T><<<(unsigned)blocks, kThreads, 0, st>>>(g, a, x, v);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partial, cudaStream_t st) {
+  k_reg_sum<T><<<kRedBlocks, kThreads, 0, st>>>(g, s, vh, partial);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_spectral<float>(const Grid&, const SpecArgs&, cx<float>*, cx<float>*, cudaStream_t);
+template cudaError_t launch_spectral<double>(const Grid&, const SpecArgs&, cx<double>*, cx<double>*, cudaStream_t);
+template cudaError_t launch_reg_sum<float>(const Grid&, int, const cx<float>*, double*, cudaStream_t);
+template cudaError_t launch_reg_sum<double>(const Grid&, int, const cx<double>*, double*, cudaStream_t);
+
+}  // namespace ga

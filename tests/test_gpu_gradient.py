@@ -1,0 +1,136 @@
+"""GPU parity of the objective, reduced gradient and preconditioner (Eqs. (1a), (3), (9)) and of
+the autograd transport wrapper, against the FP64 oracle, for the three models in 2D and 3D."""
+import numpy as np
+import pytest
+
+from gpu_util import TOL, TOL_GRAD_MIXED, empty, host, quantise, rel_l2, to_dev
+from oracle import spectral as osp
+from oracle.problem import Problem as OProblem
+from synth.inputs import random_fourier_field, random_problem_fields
+
+pytestmark = pytest.mark.gpu
+
+MODELS = ["advection", "continuity", "incompressible"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_08782_gb300 import build
+
+    build.build()
+
+
+def _setup(shape, prec, model, nt=4, s=2, alpha=1e-3, seed=0, ckpt=0):
+    from paper_2510_08782_gb300 import Problem
+
+    m0, m1, v = random_problem_fields(shape, seed, model=model, vel_scale_vox=1.5)
+    m0, m1, v = quantise(m0, prec), quantise(m1, prec), quantise(v, prec)
+    P = Problem(to_dev(m0, prec), to_dev(m1, prec), nt=nt, model=model, reg_order=s, alpha=alpha,
+                prec=prec, ckpt_every=ckpt)
+    O = OProblem(m0, m1, nt=nt, model=model, reg_order=s, alpha=alpha)
+    return P, O, v
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("shape", [(32, 24), (16, 12, 20), (24, 20, 18)])
+def test_objective_and_gradient(shape, prec, model):
+    s = 1 if model != "advection" else 2
+    P, O, v = _setup(shape, prec, model, s=s, nt=4 if len(shape) == 3 else 6)
+    g = empty(v.shape, prec)
+    J = P.gradient(to_dev(v, prec), g)
+    gref, Jref = O.gradient(v)
+    tol = TOL[prec] if prec == "fp64" else TOL_GRAD_MIXED
+    assert abs(J - Jref) <= tol * abs(Jref)
+    assert rel_l2(host(g), gref) < tol, rel_l2(host(g), gref)
+    Jo = P.objective(to_dev(v, prec))
+    assert abs(Jo - Jref) <= tol * abs(Jref)
+    s_out = empty(v.shape, prec)
+    P.precond(g, s_out)
+    assert rel_l2(host(s_out), O.precond(host(g))) < TOL[prec] * 10
+
+
+@pytest.mark.parametrize("ckpt", [1, 3, 4])
+def test_checkpointed_gradient_equals_stored(ckpt):
+    shape = (16, 12, 20)
+    P0, O, v = _setup(shape, "fp64", "continuity", nt=7, s=1)
+    Pk, _, _ = _setup(shape, "fp64", "continuity", nt=7, s=1, ckpt=ckpt)
+    g0, gk = empty(v.shape, "fp64"), empty(v.shape, "fp64")
+    J0 = P0.gradient(to_dev(v, "fp64"), g0)
+    Jk = Pk.gradient(to_dev(v, "fp64"), gk)
+    # recomputation repeats the same kernels on the same inputs: bitwise identical
+    assert J0 == Jk
+    assert np.array_equal(host(g0), host(gk))
+
+
+def test_host_buffers_match_device_buffers():
+    shape = (32, 24)
+    P, O, v = _setup(shape, "fp64", "advection")
+    g_dev = empty(v.shape, "fp64")
+    Jd = P.gradient(to_dev(v, "fp64"), g_dev)
+    g_host = np.zeros(v.shape)
+    Jh = P.gradient(np.ascontiguousarray(v), g_host)
+    assert Jd == Jh and np.array_equal(host(g_dev), g_host)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("model", ["advection", "continuity"])
+def test_autograd_transport_vjp_matches_oracle_body_force(prec, model):
+    import torch
+
+    from paper_2510_08782_gb300.autograd import transport
+
+    shape = (16, 12, 20)
+    P, O, v = _setup(shape, prec, model, nt=4)
+    vt = to_dev(v, prec).requires_grad_(True)
+    mT = transport(vt, P)
+    ref_states = O.states(v)
+    assert rel_l2(host(mT), ref_states[-1]) < TOL[prec]
+    gamma = quantise(random_fourier_field(shape, 1, 3, np.random.default_rng(9))[0], prec)
+    (mT * to_dev(gamma, prec)).sum().backward()
+    # oracle: the VJP is minus the body force with terminal adjoint value gamma
+    from oracle.transport import adjoint_states
+
+    mu = osp.div(v)
+    lams = adjoint_states(model, gamma, v, 4, mu=mu)
+    ref = np.zeros_like(v)
+    for j in range(5):
+        wj = 0.5 if j in (0, 4) else 1.0
+        if model == "continuity":
+            ref -= 0.25 * wj * ref_states[j] * osp.grad(lams[j])
+        else:
+            ref += 0.25 * wj * lams[j] * osp.grad(ref_states[j])
+    assert rel_l2(host(vt.grad), -ref) < TOL[prec] * 3
+
+
+def test_autograd_incompressible_fd_directions():
+    """Config-3 style check at a small size: autograd gradient of the full objective along random
+    divergence-free directions vs central finite differences (eps 1e-4) of the FP64 oracle objective,
+    to the discretisation error of the optimise-then-discretise gradient."""
+    import torch
+
+    from paper_2510_08782_gb300.autograd import transport
+
+    shape = (24, 20, 18)
+    P, O, v = _setup(shape, "mixed", "incompressible", nt=8, s=1, alpha=1e-2)
+    v = osp.leray(v)
+    vt = to_dev(v, "mixed").requires_grad_(True)
+    m1 = to_dev(O.m1, "mixed")
+    hd = osp.cell_volume(shape)
+    loss = 0.5 * hd * ((transport(vt, P) - m1) ** 2).sum()
+    loss.backward()
+    gdata = host(vt.grad)
+    rng = np.random.default_rng(11)
+    errs = []
+    for _ in range(4):
+        d = osp.leray(random_fourier_field(shape, 3, 4, rng))
+        d /= np.abs(d).max()
+        eps = 1e-4
+        Op = OProblem(O.m0, O.m1, nt=8, model="incompressible", reg_order=1, alpha=1e-30)
+        fd = (Op.objective(v + eps * d) - Op.objective(v - eps * d)) / (2 * eps)
+        an = float(np.sum(gdata * d))
+        errs.append(abs(fd - an) / abs(fd))
+    assert max(errs) < 0.1, errs

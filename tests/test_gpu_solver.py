@@ -1,0 +1,129 @@
+"""GPU parity of the solver (Alg. 3 with the Armijo map q of Eqs. (6)-(10)) against the oracle,
+and the error paths of the C ABI that need a device (NaN input, exhausted line search)."""
+import numpy as np
+import pytest
+
+from gpu_util import empty, host, quantise, rel_l2, to_dev
+from oracle import solver as osol
+from oracle.problem import Problem as OProblem
+from synth.inputs import random_problem_fields, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_08782_gb300 import build
+
+    build.build()
+
+
+def _pair(w, prec, **kw):
+    from paper_2510_08782_gb300 import Problem
+
+    m0, m1 = quantise(w["m0"], prec), quantise(w["m1"], prec)
+    opts = dict(nt=w["nt"], model=w["model"], reg_order=w["reg_order"], alpha=w["alpha"])
+    sopts = dict(window=w["window"], sigma=w["sigma"], tau=w["tau"], max_iter=w["max_iter"],
+                 rel_tol=w["rel_tol"])
+    sopts.update(kw)
+    P = Problem(to_dev(m0, prec), to_dev(m1, prec), prec=prec, **opts, **sopts)
+    O = OProblem(m0, m1, **opts)
+    return P, O, sopts
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_iterates_match_oracle_fp64(variant):
+    """First iterates of GA-NGMRES(5; 2, 1) (both mixing variants) on a small 2D advection problem:
+    line-search decisions, window least squares and combination reproduce the oracle's iterates."""
+    w = workload("adv2d64", n=(32, 32))
+    P, O, so = _pair(w, "fp64", window=3, sigma=2, tau=1, max_iter=8, variant=variant)
+    v = to_dev(np.zeros((2, 32, 32)), "fp64")
+    hist = []
+    q = osol.ArmijoQ(O)
+    osol.ga_ngmres(O.gradient, q, np.zeros((2, 32, 32)), window=3, sigma=2, tau=1, n_iter=6,
+                   rel_tol=0.0, variant=variant, history=hist)
+    for k, h in enumerate(hist):
+        st = P.step(v)
+        assert st.iters == k + 1
+        assert st.last_branch == (1 if h["branch"] == "fp" else 0)
+        err = rel_l2(host(v), h["v"])
+        assert err < 1e-8, (k, err)
+        assert abs(st.obj - h["obj"]) <= 1e-9 * abs(h["obj"])
+    assert abs(st.rho_mem - q.rho_mem) == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_solve_matches_oracle_adv2d64(prec):
+    """2D 64x64 advection workload (8 blobs, H1, alpha 1e-2, w 5, (4,2)), solved to rel-grad 1e-2."""
+    w = workload("adv2d64")
+    P, O, so = _pair(w, prec, max_iter=40)
+    _, info = osol.solve_problem(O, window=5, sigma=4, tau=2, n_iter=40, rel_tol=1e-2)
+    v = to_dev(np.zeros((2, 64, 64)), prec)
+    st, status = P.solve(v)
+    assert status == 0 and st.converged
+    assert abs(st.iters - info["iters"]) <= (0 if prec == "fp64" else 2)
+    assert st.rel_grad_inf <= 1e-2
+    tol = 1e-6 if prec == "fp64" else 1e-3
+    assert abs(st.obj - info["obj"]) <= tol * abs(info["obj"])
+
+
+def test_rpgd_is_slower_than_ga_ngmres_on_gpu():
+    w = workload("adv2d64")
+    P1, _, _ = _pair(w, "fp64", max_iter=60)
+    P2, _, _ = _pair(w, "fp64", max_iter=60, method="rpgd")
+    v1 = to_dev(np.zeros((2, 64, 64)), "fp64")
+    v2 = to_dev(np.zeros((2, 64, 64)), "fp64")
+    s1, _ = P1.solve(v1)
+    s2, _ = P2.solve(v2)
+    assert s1.converged and s1.iters < s2.iters
+
+
+def test_nan_input_is_reported():
+    from paper_2510_08782_gb300 import GaError
+
+    w = workload("adv2d64", n=(16, 16))
+    P, _, _ = _pair(w, "fp64")
+    v = np.zeros((2, 16, 16))
+    v[0, 3, 4] = np.nan
+    g = empty(v.shape, "fp64")
+    with pytest.raises(GaError) as e:
+        P.gradient(to_dev(v, "fp64"), g)
+    assert e.value.status == 4
+    # the context stays usable
+    J = P.gradient(to_dev(np.zeros_like(v), "fp64"), g)
+    assert np.isfinite(J)
+
+
+def test_exhausted_line_search_is_reported():
+    from paper_2510_08782_gb300 import GaError
+
+    w = workload("adv2d64", n=(16, 16))
+    P, _, _ = _pair(w, "fp64", armijo_c=1e30, max_backtracks=3)
+    v = to_dev(np.zeros((2, 16, 16)), "fp64")
+    with pytest.raises(GaError) as e:
+        P.step(v)
+    assert e.value.status == 5
+    assert "Armijo" in str(e.value)
+
+
+def test_batch_of_uneven_problems_matches_individual_solves():
+    from paper_2510_08782_gb300 import ga_solve_batch
+
+    probs, vs, refs = [], [], []
+    for i, n in enumerate([(16, 16, 16), (24, 24, 24), (20, 20, 20)]):
+        m0, m1, _ = random_problem_fields(n, 40 + i, vel_scale_vox=1.0)
+        w = dict(m0=m0, m1=m1, nt=4, model="advection", reg_order=1, alpha=1e-2, window=5, sigma=4,
+                 tau=2, max_iter=15, rel_tol=1e-2)
+        P, _, _ = _pair(w, "mixed")
+        Q, _, _ = _pair(w, "mixed")
+        probs.append(P)
+        vs.append(to_dev(np.zeros((3,) + n), "mixed"))
+        vq = to_dev(np.zeros((3,) + n), "mixed")
+        refs.append((Q.solve(vq)[0], vq))
+    stats, status = ga_solve_batch([p.ctx for p in probs], np.float32, vs)
+    for st, (ref, vq), v in zip(stats, refs, vs):
+        assert st.iters == ref.iters
+        assert np.array_equal(host(v), host(vq))
