@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the GA-NGMRES gradient-evaluation hot path on one GB300 per process.
+
+Workload: 3D 256^3 mass-preserving (continuity) model, n_t = 16, H1 regularisation alpha = 1e-3,
+GA-NGMRES(10; 4, 2), trajectory checkpointing every 4 steps, FP32 fields with FP64 reductions, inputs
+= 64 anisotropic Gaussians (densities) displaced by a smooth velocity of up to 6 voxels (seeded,
+synthetic). One step = one GA-NGMRES iteration (ga_step): preconditioner, Armijo line search (state
+solves), reduced gradient(s) (state + adjoint solves, body force, spectral epilogue), window inner
+products, least squares, combination and stop test.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). `value` is gradient evaluations per second over all ranks (each rank
+runs an independent replica: the problem does not shard), `e2e` the same through host buffers,
+`tts_s` the time to relative gradient 1e-2 from v = 0. The reference arm times the FP64 NumPy oracle
+on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "gradient evals/s & GA-NGMRES time to rel-grad 1e-2 at 256^3; HBM roofline frac"
+UNIT = "grad_evals/s"
+N = 256
+NT = 16
+SETTINGS = dict(nt=NT, model="continuity", reg_order=1, alpha=1e-3, ckpt_every=4, window=10, sigma=4,
+                tau=2, max_iter=200, rel_tol=1e-2)
+WORKLOAD_NAME = ("cont3d256: 256^3 continuity (mass-preserving), nt=16, H1 alpha=1e-3, "
+                 "GA-NGMRES(10;4,2), checkpoint every 4, 64 anisotropic Gaussian densities, 6-voxel velocity")
+CPU_SAMPLE_N = 48  # oracle sample grid (same recipe), scaled to 256^3 by voxel count
+
+# kernel classes timed with events inside the library (ga_prof_start)
+PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ = 0, 1, 2, 3
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(n=N, seed=0):
+    from synth.inputs import workload
+
+    return workload("cont3d256", seed=seed, n=(n, n, n))
+
+
+def cpu_baseline(steps=1, warmup=0, n=CPU_SAMPLE_N):
+    """The FP64 oracle's reduced gradient on an n^3 sample of the same recipe, scaled to 256^3."""
+    from oracle.problem import Problem as OProblem
+
+    w = make_inputs(n)
+    P = OProblem(w["m0"], w["m1"], nt=NT, model="continuity", reg_order=1, alpha=1e-3)
+    v = np.zeros((3, n, n, n))
+    for _ in range(warmup):
+        P.gradient(v)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        P.gradient(v)
+    dt = (time.perf_counter() - t0) / steps
+    scale = (N / n) ** 3
+    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle reduced-gradient evaluation(s) of the same recipe at {n}^3 "
+                      f"(nt=16), {dt:.2f} s each, scaled to 256^3 by voxel count x{scale:.0f}; "
+                      "NumPy single-threaded (gathers and pocketfft)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline(steps=args.steps, warmup=args.warmup)
+    dt_step = 1.0 / (cb["value"] * (N / CPU_SAMPLE_N) ** 3)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tts", action="store_true")
+    ap.add_argument("--prof-class", type=int, default=PROF_SL_FWD)
+    ap.add_argument("--grid", type=int, default=N, help="grid size (default 256; smaller only for smoke runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2510_08782_gb300 as ga
+    from paper_2510_08782_gb300 import build
+
+    ws, rank, local = dist_env()
+    build.build()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.grid
+    w = make_inputs(n)
+    shape = (n, n, n)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    m0, m1 = dev(w["m0"]), dev(w["m1"])
+    P = ga.Problem(m0, m1, prec="mixed", **SETTINGS)
+    v = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up (W GA-NGMRES iterations from v = 0) ----
+    for _ in range(args.warmup):
+        P.step(v)
+    # ---- timed: K iterations of a fresh solve from v = 0 ----
+    P.reset()
+    v.zero_()
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except Exception:
+            pass
+    sampler = ClockSampler(gpu_index)
+    barrier()
+    launches0 = ga.ga_kernel_launches()
+    ga.ga_prof_start(P.ctx, args.prof_class)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = None
+    for _ in range(args.steps):
+        st = P.step(v)
+    e1.record()
+    barrier()
+    clocks = sampler.stop()
+    prof_ms, prof_n = ga.ga_prof_stop(P.ctx)
+    launches = ga.ga_kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    grad_evals = st.grad_evals
+    if ws > 1:
+        t = torch.tensor([ms, float(grad_evals)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        ms_max, total_evals = float(tmax[0]), float(tsum[1])
+    else:
+        ms_max, total_evals = ms, float(grad_evals)
+    value = total_evals / (ms_max / 1e3)
+    step_stats = st.as_dict()
+
+    # ---- roofline of the dominant kernel: algorithmic bytes per launch / mean event duration ----
+    nv = n ** 3
+    algo = {PROF_SL_FWD: ("sl_forward continuity step: read pi_j, mu, 3 displacement fields, write pi_{j+1}", 24),
+            PROF_SL_ADJ: ("sl_adjoint continuity step: read lambda_{j+1}, 3 displacement fields, write lambda_j", 20),
+            PROF_DERIV: ("fused FFT-derivative pass: read f, read multiplier, read+write accumulator", 16),
+            PROF_FFT: ("3D real FFT (3 passes)", 24)}[args.prof_class]
+    hbm, peak_kind = peaks()
+    per_launch_ms = prof_ms / max(prof_n, 1)
+    bytes_per_launch = algo[1] * nv
+    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None, "kernel": algo[0],
+                "bytes_per_launch": bytes_per_launch, "launches": prof_n, "mean_launch_ms": per_launch_ms,
+                "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"}
+
+    # ---- time to rel-grad 1e-2 from v = 0 (GA-NGMRES) ----
+    tts = None
+    if not args.no_tts:
+        P.reset()
+        v.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        try:
+            stt, status = P.solve(v)
+            err = None
+        except ga.GaError as e:  # e.g. an exhausted line search: report it with the last statistics
+            err = str(e)
+            stt = ga.Stats()
+            ga.lib().ga_get_stats(P.ctx, stt)
+        torch.cuda.synchronize()
+        tts = {"tts_s": time.perf_counter() - t0, "iters": stt.iters, "converged": bool(stt.converged),
+               "rel_grad_inf": stt.rel_grad_inf, "grad_evals": stt.grad_evals, "obj_evals": stt.obj_evals,
+               "pde_solves": stt.pde_solves, "mismatch": stt.mismatch, "obj": stt.obj, "error": err}
+
+    # ---- pure gradient throughput (ga_gradient only) ----
+    g = torch.empty_like(v)
+    P.gradient(v, g)
+    torch.cuda.synchronize()
+    e0.record()
+    reps = 5
+    for _ in range(reps):
+        P.gradient(v, g)
+    e1.record()
+    torch.cuda.synchronize()
+    grad_only = reps / (e0.elapsed_time(e1) / 1e3)
+
+    # ---- end to end through host buffers: setup from host m0/m1, K steps with a host v ----
+    e2e = None
+    if not args.no_e2e:
+        P.close()
+        del P
+        torch.cuda.empty_cache()
+        hm0 = torch.from_numpy(np.ascontiguousarray(w["m0"], dtype=np.float32)).pin_memory()
+        hm1 = torch.from_numpy(np.ascontiguousarray(w["m1"], dtype=np.float32)).pin_memory()
+        hv = torch.zeros((3,) + shape, dtype=torch.float32).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        Q = ga.Problem(hm0, hm1, prec="mixed", **SETTINGS)
+        for _ in range(args.steps):
+            sq = Q.step(hv)
+        Q.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t[0])
+        e2e = {"value": ws * sq.grad_evals / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int((2 * nv + 3 * nv) * 4 / args.steps),
+               "d2h_bytes_per_step": int(3 * nv * 4),
+               "note": "timed: ga_setup from pinned host m0/m1 + K ga_step calls with a pinned host v "
+                       "(v^(0) uploaded once, v^(k+1) read back every step) + ga_destroy; "
+                       "h2d bytes are the job's uploads divided by K"}
+    cb = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAME, "grid": [n, n, n], "nt": NT, "precision":
+                           "FP32 fields/transport/FFT, FP64 compensated reductions, Gram and least squares",
+                           "step": "one GA-NGMRES iteration (ga_step) of a solve from v=0",
+                           "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
+                           "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "tts": tts, "grad_only_evals_per_s": grad_only,
+                "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in
+                                                                       ("iters", "obj_evals", "rel_grad_inf", "obj",
+                                                                        "rho_mem")}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

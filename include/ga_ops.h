@@ -79,11 +79,15 @@ ga_status ga_transport(ga_ctx* ctx, const void* v, void* m1_out, int mem);
 ga_status ga_transport_vjp(ga_ctx* ctx, const void* v, const void* gamma, void* grad_v, int mem);
 
 /* Device-time accounting of one kernel class over a region of calls, with CUDA events recorded
- * on the context stream around every launch of that class: 0 = semi-Lagrangian state/adjoint
- * steps, 1 = fused FFT-derivative passes, 2 = 3D FFT passes. ga_prof_stop returns the summed
- * event time (ms) and the number of launches since ga_prof_start, and ends the accounting. */
+ * on the context stream around every launch of that class: 0 = semi-Lagrangian state steps,
+ * 1 = fused FFT-derivative passes, 2 = 3D FFT transforms (all passes of one transform),
+ * 3 = semi-Lagrangian adjoint steps. ga_prof_stop returns the summed event time (ms) and the
+ * number of timed launches since ga_prof_start, and ends the accounting. */
 ga_status ga_prof_start(ga_ctx* ctx, int kernel_class);
 ga_status ga_prof_stop(ga_ctx* ctx, double* total_ms, long long* launches);
+
+/* Number of CUDA kernels the library has launched in this process so far (all contexts). */
+long long ga_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -90,6 +90,7 @@ _SIGS = {
     "ga_transport_vjp": ([_vp, _vp, _vp, _vp, _c_int], _c_int),
     "ga_prof_start": ([_vp, _c_int], _c_int),
     "ga_prof_stop": ([_vp, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)], _c_int),
+    "ga_kernel_launches": ([], ctypes.c_longlong),
 }
 
 
@@ -310,6 +311,11 @@ def ga_op_lsq(ctx, c, a, M):
 
 def ga_prof_start(ctx, kernel_class):
     _check(lib().ga_prof_start(ctx, int(kernel_class)), ctx)
+
+
+def ga_kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(lib().ga_kernel_launches())
 
 
 def ga_prof_stop(ctx):

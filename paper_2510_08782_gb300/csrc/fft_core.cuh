@@ -104,6 +104,34 @@ GA_HD void stockham_butterfly(const cx<T>* in, cx<T>* out, int j, int N, int R, 
   for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
 }
 
+// Compile-time variant of one stage for a fixed length N, radix R and span Ns: every index
+// operation folds to constants (shifts and masks for powers of two).
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+constexpr int ct_next_radix(int rem) {
+  return rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : (rem % 3 == 0 ? 3 : 5)));
+}
+
+template <typename T, int N, int R, int Ns>
+GA_HD void stockham_butterfly_ct(const cx<T>* in, cx<T>* out, int j, const cx<T>* tw) {
+  constexpr int M = N / R;
+  const int k = j % Ns;
+  const int tstep = k * (N / (Ns * R));
+  cx<T> v[R];
+  v[0] = in[j];
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * M], tw[r * tstep]);
+  if constexpr (R == 2) dft2(v);
+  else if constexpr (R == 3) dft3<T>(v);
+  else if constexpr (R == 4) dft4(v);
+  else if constexpr (R == 5) dft5<T>(v);
+  else dft8<T>(v);
+  const int base = (j - k) * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+}
+
 // Host: factor N into radices (8s first for powers of two, then 4/2, 3, 5). Returns false if N
 // has a prime factor other than 2, 3, 5 or if N < 1.
 inline bool make_plan(int N, FftPlan* p) {

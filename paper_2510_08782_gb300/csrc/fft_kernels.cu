@@ -13,6 +13,8 @@
 // transforms of the other axes cancel), so d/dx_c costs one pass, not a 3D FFT.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "kernels.h"
 
@@ -20,9 +22,32 @@ namespace ga {
 
 namespace {
 
-template <typename T>
+// Compile-time stage sequence for a fixed length N (radices from ct_next_radix).
+template <typename T, int N, int Ns> struct CtStages {
+  __device__ __forceinline__ static cx<T>* run(cx<T>* a, cx<T>* b, int B, int ld, const cx<T>* tw) {
+    if constexpr (Ns >= N) {
+      return a;
+    } else {
+      constexpr int R = ct_next_radix(N / Ns);
+      constexpr int M = N / R;
+      const int total = B * M;
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int p = t / M;
+        const int j = t - p * M;
+        stockham_butterfly_ct<T, N, R, Ns>(a + p * ld, b + p * ld, j, tw);
+      }
+      __syncthreads();
+      return CtStages<T, N, Ns * R>::run(b, a, B, ld, tw);
+    }
+  }
+};
+
+template <typename T, int NC>
 __device__ cx<T>* run_fft(cx<T>* a, cx<T>* b, int N, int B, int ld, const FftPlan& plan,
                           const cx<T>* tw) {
+  if constexpr (NC > 0) {
+    return CtStages<T, NC, 1>::run(a, b, B, ld, tw);
+  }
   int Ns = 1;
   for (int s = 0; s < plan.ns; ++s) {
     const int R = plan.radix[s];
@@ -64,7 +89,7 @@ template <typename T> __device__ __forceinline__ void load_tw(cx<T>* tw, const c
 }
 
 // ---- derivative along the contiguous axis (rows) --------------------------------------------
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
              int accumulate, long long rows, int L, int B, int ld, FftPlan plan,
@@ -82,10 +107,10 @@ k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
     reinterpret_cast<T*>(&a[(rr >> 1) * ld + j])[rr & 1] = val;
   }
   __syncthreads();
-  cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
   cx<T>* o = (r == a) ? b : a;
   mult_ik_conj<T>(r, B, L, ld);
-  cx<T>* r2 = run_fft<T>(r, o, L, B, ld, plan, tw);
+  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, tw);
   const T inv = T(1) / T(L);
   for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
     const int rr = idx / L, j = idx - rr * L;
@@ -101,7 +126,7 @@ k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
 }
 
 // ---- derivative along a strided axis (tiles of 2B adjacent columns) ---------------------------
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
              int accumulate, int L, long long S, long long outer_stride, int nx, int B, int ld,
@@ -120,10 +145,10 @@ k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
     reinterpret_cast<T*>(&a[(xx >> 1) * ld + j])[xx & 1] = val;
   }
   __syncthreads();
-  cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
   cx<T>* o = (r == a) ? b : a;
   mult_ik_conj<T>(r, B, L, ld);
-  cx<T>* r2 = run_fft<T>(r, o, L, B, ld, plan, tw);
+  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, tw);
   const T inv = T(1) / T(L);
   for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
     const int j = idx / W, xx = idx - j * W;
@@ -138,7 +163,7 @@ k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
 }
 
 // ---- real-to-complex FFT of row pairs ---------------------------------------------------------
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_r2c_rows(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, int L, int Lh, int B,
            int ld, FftPlan plan, const cx<T>* __restrict__ twg) {
@@ -155,7 +180,7 @@ k_r2c_rows(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, int 
     reinterpret_cast<T*>(&a[(rr >> 1) * ld + j])[rr & 1] = val;
   }
   __syncthreads();
-  const cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  const cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
   for (int idx = threadIdx.x; idx < B * Lh; idx += blockDim.x) {
     const int p = idx / Lh, k = idx - p * Lh;
     const cx<T> zk = r[p * ld + k];
@@ -169,7 +194,7 @@ k_r2c_rows(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, int 
 }
 
 // ---- complex-to-real inverse FFT of row pairs (normalised by `scale`) --------------------------
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_c2r_rows(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, int L, int Lh, int B,
            int ld, FftPlan plan, const cx<T>* __restrict__ twg, T scale) {
@@ -198,7 +223,7 @@ k_c2r_rows(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, int 
     }
   }
   __syncthreads();
-  const cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  const cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
   for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
     const int rr = idx / L, j = idx - rr * L;
     const long long row = row0 + rr;
@@ -209,7 +234,7 @@ k_c2r_rows(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, int 
 }
 
 // ---- complex FFT along a strided axis of the half spectrum, in place ---------------------------
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_fft_cols(cx<T>* __restrict__ fh, int L, long long S, long long outer_stride, int nx, int B, int ld,
            FftPlan plan, const cx<T>* __restrict__ twg, int inverse, T scale) {
@@ -227,7 +252,7 @@ k_fft_cols(cx<T>* __restrict__ fh, int L, long long S, long long outer_stride, i
     a[p * ld + j] = z;
   }
   __syncthreads();
-  const cx<T>* r = run_fft<T>(a, b, L, B, ld, plan, tw);
+  const cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
   for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
     const int j = idx / B, p = idx - j * B;
     if (x0 + p >= nx) continue;
@@ -246,6 +271,22 @@ template <typename T> int batch_for(int L) {
 inline int lead_dim(int L) { return (L % 2 == 0) ? L + 1 : L; }
 template <typename T> size_t smem_bytes(int L, int B) {
   return sizeof(cx<T>) * ((size_t)L + 2 * (size_t)B * lead_dim(L));
+}
+
+// Calls f(std::integral_constant<int, NC>) with NC = L for the FP32 lengths that have a compile-time
+// plan, else NC = 0 (runtime plan).
+template <typename T, typename F> cudaError_t with_nc(int L, F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    switch (L) {
+      case 64: return f(std::integral_constant<int, 64>());
+      case 96: return f(std::integral_constant<int, 96>());
+      case 128: return f(std::integral_constant<int, 128>());
+      case 160: return f(std::integral_constant<int, 160>());
+      case 256: return f(std::integral_constant<int, 256>());
+      default: break;
+    }
+  }
+  return f(std::integral_constant<int, 0>());
 }
 
 template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
@@ -270,18 +311,20 @@ cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const 
     const long long pairs = (rows + 1) / 2;
     if (B > pairs) B = (int)pairs;
     const size_t sm = smem_bytes<T>(L, B);
-    cudaError_t e = allow_smem(k_deriv_rows<T>, sm);
-    if (e != cudaSuccess) return e;
     const long long grid = (rows + 2LL * B - 1) / (2LL * B);
-    k_deriv_rows<T><<<(unsigned)grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, rows,
-                                                           L, B, ld, ft.plan[2], ft.tw[2]);
-    return cudaGetLastError();
+    return with_nc<T>(L, [&](auto nc) {
+      constexpr int NC = decltype(nc)::value;
+      cudaError_t e = allow_smem(k_deriv_rows<T, NC>, sm);
+      if (e != cudaSuccess) return e;
+      note_launches(1);
+      k_deriv_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, rows,
+                                                                 L, B, ld, ft.plan[2], ft.tw[2]);
+      return cudaGetLastError();
+    });
   }
   const int nx = g.n[2];
   if (2 * B > nx) B = (nx + 1) / 2;
   const size_t sm = smem_bytes<T>(L, B);
-  cudaError_t e = allow_smem(k_deriv_cols<T>, sm);
-  if (e != cudaSuccess) return e;
   long long S, outer_stride;
   int outer;
   if (axis == 1) {
@@ -294,9 +337,15 @@ cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const 
     outer_stride = nx;
   }
   dim3 grid((nx + 2 * B - 1) / (2 * B), outer);
-  k_deriv_cols<T><<<grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, L, S, outer_stride,
-                                               nx, B, ld, ft.plan[axis], ft.tw[axis]);
-  return cudaGetLastError();
+  return with_nc<T>(L, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    cudaError_t e = allow_smem(k_deriv_cols<T, NC>, sm);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    k_deriv_cols<T, NC><<<grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, L, S, outer_stride,
+                                                     nx, B, ld, ft.plan[axis], ft.tw[axis]);
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
@@ -309,8 +358,6 @@ static cudaError_t launch_cols(const Grid& g, const FftTables<T>& ft, int axis, 
   if (B > nx) B = nx;
   const int ld = lead_dim(L);
   const size_t sm = smem_bytes<T>(L, B);
-  cudaError_t e = allow_smem(k_fft_cols<T>, sm);
-  if (e != cudaSuccess) return e;
   long long S, outer_stride;
   int outer;
   if (axis == 1) {
@@ -323,9 +370,15 @@ static cudaError_t launch_cols(const Grid& g, const FftTables<T>& ft, int axis, 
     outer_stride = nx;
   }
   dim3 grid((nx + B - 1) / B, outer);
-  k_fft_cols<T><<<grid, kThreads, sm, st>>>(fh, L, S, outer_stride, nx, B, ld, ft.plan[axis], ft.tw[axis],
-                                             inverse, T(1) / T(L));
-  return cudaGetLastError();
+  return with_nc<T>(L, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    cudaError_t e = allow_smem(k_fft_cols<T, NC>, sm);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    k_fft_cols<T, NC><<<grid, kThreads, sm, st>>>(fh, L, S, outer_stride, nx, B, ld, ft.plan[axis], ft.tw[axis],
+                                                   inverse, T(1) / T(L));
+    return cudaGetLastError();
+  });
 }
 
 template <typename T>
@@ -336,11 +389,16 @@ cudaError_t launch_r2c(const Grid& g, const FftTables<T>& ft, const T* f, cx<T>*
   if (B > (rows + 1) / 2) B = (int)((rows + 1) / 2);
   const int ld = lead_dim(L);
   const size_t sm = smem_bytes<T>(L, B);
-  cudaError_t e = allow_smem(k_r2c_rows<T>, sm);
-  if (e != cudaSuccess) return e;
   const long long grid = (rows + 2LL * B - 1) / (2LL * B);
-  k_r2c_rows<T><<<(unsigned)grid, kThreads, sm, st>>>(f, fh, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2]);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaError_t e = with_nc<T>(L, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    cudaError_t e2 = allow_smem(k_r2c_rows<T, NC>, sm);
+    if (e2 != cudaSuccess) return e2;
+    note_launches(1);
+    k_r2c_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(f, fh, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2]);
+    return cudaGetLastError();
+  });
+  if (e != cudaSuccess) return e;
   if ((e = launch_cols<T>(g, ft, 1, fh, 0, st)) != cudaSuccess) return e;
   return launch_cols<T>(g, ft, 0, fh, 0, st);
 }
@@ -356,11 +414,16 @@ cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, c
   if (B > (rows + 1) / 2) B = (int)((rows + 1) / 2);
   const int ld = lead_dim(L);
   const size_t sm = smem_bytes<T>(L, B);
-  if ((e = allow_smem(k_c2r_rows<T>, sm)) != cudaSuccess) return e;
   const long long grid = (rows + 2LL * B - 1) / (2LL * B);
-  k_c2r_rows<T><<<(unsigned)grid, kThreads, sm, st>>>(fh, f, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2],
-                                                       T(1) / T(L));
-  return cudaGetLastError();
+  return with_nc<T>(L, [&](auto nc) {
+    constexpr int NC = decltype(nc)::value;
+    cudaError_t e2 = allow_smem(k_c2r_rows<T, NC>, sm);
+    if (e2 != cudaSuccess) return e2;
+    note_launches(1);
+    k_c2r_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(fh, f, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2],
+                                                             T(1) / T(L));
+    return cudaGetLastError();
+  });
 }
 
 #define GA_INST(T)                                                                                  \

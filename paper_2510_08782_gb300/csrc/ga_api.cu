@@ -28,6 +28,13 @@
 
 using namespace ga;
 
+#include <atomic>
+
+namespace ga {
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace ga
+
 namespace {
 
 constexpr int kNumRes = 64;  // device FP64 result slots
@@ -216,7 +223,7 @@ template <typename T> struct Engine : EngineBase {
   }
 
   // ---- profiling hooks ------------------------------------------------------------------------
-  enum { PROF_SL = 0, PROF_DERIV = 1, PROF_FFT = 2 };
+  enum { PROF_SL_FWD = 0, PROF_DERIV = 1, PROF_FFT = 2, PROF_SL_ADJ = 3 };
   void prof_begin(int cls) {
     if (prof_class != cls) return;
     if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
@@ -249,14 +256,14 @@ template <typename T> struct Engine : EngineBase {
   bool stored(int j) const { return K == 0 || j % K == 0 || j == nt; }
 
   void sl_forward(const T* src, T* dst) {
-    prof_begin(PROF_SL);
+    prof_begin(PROF_SL_FWD);
     ck(launch_sl_forward<T>(g, model == GA_MODEL_CONTINUITY, src, xm, mu, dst, (T)ht, st), "sl_forward");
-    prof_end(PROF_SL);
+    prof_end(PROF_SL_FWD);
   }
   void sl_adjoint(const T* src, T* dst) {
-    prof_begin(PROF_SL);
+    prof_begin(PROF_SL_ADJ);
     ck(launch_sl_adjoint<T>(g, model == GA_MODEL_CONTINUITY, src, xp, mu, dst, (T)ht, st), "sl_adjoint");
-    prof_end(PROF_SL);
+    prof_end(PROF_SL_ADJ);
   }
   void deriv(int axis, const T* f, const T* mult, T* out, double coef, bool acc) {
     prof_begin(PROF_DERIV);
@@ -964,8 +971,10 @@ ga_status ga_transport_vjp(ga_ctx* ctx, const void* v, const void* gamma, void* 
 }
 
 // ---- event timing of one kernel class over a region (used by the benchmark) --------------------------
+long long ga_kernel_launches(void) { return ga::g_launches.load(std::memory_order_relaxed); }
+
 ga_status ga_prof_start(ga_ctx* ctx, int kernel_class) {
-  if (!ctx || kernel_class < 0 || kernel_class > 2) return GA_ERR_ARG;
+  if (!ctx || kernel_class < 0 || kernel_class > 3) return GA_ERR_ARG;
   return dispatch(ctx, [&](auto& e) {
     if (e.prof_ev.empty()) {
       e.prof_ev.resize(4096);

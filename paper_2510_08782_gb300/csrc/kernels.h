@@ -15,6 +15,9 @@ constexpr int kMaxWin = 31;         // window entries in the least-squares kerne
 
 template <typename T> struct PtrList { const T* p[16]; };
 
+// Counts kernel launches issued by the library (process-wide).
+void note_launches(int n);
+
 template <typename T> struct FftTables {
   FftPlan plan[3];
   const cx<T>* tw[3];  // device tables exp(-2 pi i m / n_a), m < n_a
@@ -57,6 +60,9 @@ cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cuda
 template <typename T>
 cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T* xm, const T* mu,
                               T* out, T ht, cudaStream_t st);
+// Tiled FP32 3D state (adjoint = 0) or adjoint (adjoint = 1) step (sl_tile_kernels.cu).
+cudaError_t launch_sl_tile(const Grid& g, int adjoint, int continuity, const float* f, const float* disp,
+                           const float* mu, float* out, float ht, cudaStream_t st);
 // One adjoint step lambda_j from lambda_{j+1} (advection: with the source lambda div v).
 template <typename T>
 cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const T* xp, const T* mu,

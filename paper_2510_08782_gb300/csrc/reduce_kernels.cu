@@ -99,18 +99,16 @@ k_dots(const T* __restrict__ a, PtrList<T> b, int count, long long len, double* 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_maxabs(const T* __restrict__ x, long long len, double* __restrict__ partial) {
-  double m = 0.0;
+  T m = T(0);  // max of |x| is exact in the element type
   int bad = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (long long)gridDim.x * blockDim.x) {
-    const double v = fabs((double)x[i]);
-    if (!(v <= 1.0e300)) bad = 1;  // NaN or Inf
-    m = fmax(m, v);
+    const T v = fabs(x[i]);
+    if (!(v <= T(3.0e38))) bad = 1;  // NaN or Inf
+    else m = v > m ? v : m;
   }
-  if (bad) m = __longlong_as_double(0x7ff8000000000000LL);  // propagate NaN
-  // fmax drops NaN, so carry it explicitly through the block maximum
   const int anybad = __syncthreads_or(bad);
-  const double r = block_max(bad ? 0.0 : m);
+  const double r = block_max((double)m);
   if (threadIdx.x == 0) partial[blockIdx.x] = anybad ? __longlong_as_double(0x7ff8000000000000LL) : r;
 }
 
@@ -130,19 +128,22 @@ k_mismatch(const T* __restrict__ mT, const T* __restrict__ m1, T* __restrict__ l
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// out[k] = sum_b partial[k * nblocks + b] in a fixed order (Neumaier), k < count.
+// out[k] = sum_b partial[k * nblocks + b], k < count: one warp per output, each lane sums a fixed
+// strided subset in FP64 (Neumaier), then a fixed shuffle tree; deterministic.
 __global__ void k_sum_partials(const double* __restrict__ partial, int count, int nblocks,
                                double* __restrict__ out) {
-  const int k = threadIdx.x;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= count) return;
   double s = 0.0, c = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
+  for (int b = lane; b < nblocks; b += 32) {
     const double p = partial[(long long)k * nblocks + b];
     const double t = s + p;
     c += (fabs(s) >= fabs(p)) ? (s - t) + p : (p - t) + s;
     s = t;
   }
-  out[k] = s + c;
+  s += c;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) out[k] = s;
 }
 
 __global__ void k_max_partials(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
@@ -287,6 +288,7 @@ cudaError_t launch_dots(const T* a, const T* const* b, int count, long long len,
     PtrList<T> pl;
     const int cnt = (count - base) < 16 ? (count - base) : 16;
     for (int k = 0; k < 16; ++k) pl.p[k] = k < cnt ? b[base + k] : nullptr;
+    note_launches(1);
     if (cnt <= 4)
       k_dots<T, 4><<<kRedBlocks, kThreads, 0, st>>>(a, pl, cnt, len, partial + (long long)base * kRedBlocks);
     else if (cnt <= 8)
@@ -296,13 +298,16 @@ cudaError_t launch_dots(const T* a, const T* const* b, int count, long long len,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_sum_partials<<<1, 32, 0, st>>>(partial, count, kRedBlocks, out);
+  note_launches(1);
+  k_sum_partials<<<1, 32 * count, 0, st>>>(partial, count, kRedBlocks, out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_maxabs(const T* x, long long len, double* partial, double* out, cudaStream_t st) {
+  note_launches(1);
   k_maxabs<T><<<kRedBlocks, kThreads, 0, st>>>(x, len, partial);
+  note_launches(1);
   k_max_partials<<<1, kThreads, 0, st>>>(partial, kRedBlocks, out);
   return cudaGetLastError();
 }
@@ -310,18 +315,22 @@ cudaError_t launch_maxabs(const T* x, long long len, double* partial, double* ou
 template <typename T>
 cudaError_t launch_mismatch(const T* mT, const T* m1, T* lam, long long len, double* partial, double* out,
                             cudaStream_t st) {
+  note_launches(1);
   k_mismatch<T><<<kRedBlocks, kThreads, 0, st>>>(mT, m1, lam, len, partial);
+  note_launches(1);
   k_sum_partials<<<1, 32, 0, st>>>(partial, 1, kRedBlocks, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum_partials(const double* partial, int count, int nblocks, double* out, cudaStream_t st) {
-  k_sum_partials<<<1, 32, 0, st>>>(partial, count, nblocks, out);
+  note_launches(1);
+  k_sum_partials<<<1, 32 * count, 0, st>>>(partial, count, nblocks, out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_axpy(T* y, const T* x, const T* s, double a, long long len, cudaStream_t st) {
+  note_launches(1);
   k_axpy<T><<<grid_for(len), kThreads, 0, st>>>(y, x, s, (T)a, len);
   return cudaGetLastError();
 }
@@ -334,6 +343,7 @@ cudaError_t launch_combine(T* out, const T* q, const T* const* v, const double* 
     PtrList<T> pl;
     const int cnt = (m - base) < 16 ? (m - base) : 16;
     for (int k = 0; k < 16; ++k) pl.p[k] = k < cnt ? v[base + k] : nullptr;
+    note_launches(1);
     k_combine<T><<<grid_for(len), kThreads, 0, st>>>(out, q, pl, beta + base, cnt, base > 0 ? 1 : 0, len);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -344,11 +354,13 @@ cudaError_t launch_combine(T* out, const T* q, const T* const* v, const double* 
 cudaError_t launch_lsq(int m, const double* dots, const double* M, int ldm, double* beta, double* info,
                        cudaStream_t st) {
   if (m < 1 || m > kMaxWin) return cudaErrorInvalidValue;
+  note_launches(1);
   k_lsq<<<1, 32, 0, st>>>(m, dots, M, ldm, beta, info);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_push(double* M, int ldm, int mkeep, const double* row, cudaStream_t st) {
+  note_launches(1);
   k_gram_push<<<1, 32, 0, st>>>(M, ldm, mkeep, row);
   return cudaGetLastError();
 }

@@ -12,6 +12,8 @@
 //   adjoint, continuity l_j = I[l_{j+1}](X+)
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace ga {
@@ -187,6 +189,7 @@ inline unsigned grid_for(long long n) {
 
 template <typename T>
 cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cudaStream_t st) {
+  note_launches(1);
   if (g.dim == 3)
     k_departure<T, 3><<<grid_for(g.nvox), kThreads, 0, st>>>(g, v, xm, xp, ht);
   else
@@ -197,13 +200,28 @@ cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cuda
 template <typename T>
 cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T* xm, const T* mu, T* out,
                               T ht, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.dim == 3) return launch_sl_tile(g, 0, continuity, m, xm, mu, out, ht, st);
+  }
   const unsigned gr = grid_for(g.nvox);
   if (g.dim == 3) {
-    if (continuity) k_sl_forward<T, 3, 1><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
-    else k_sl_forward<T, 3, 0><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
+    if (continuity) {
+      note_launches(1);
+      k_sl_forward<T, 3, 1><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
+    }
+    else {
+      note_launches(1);
+      k_sl_forward<T, 3, 0><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
+    }
   } else {
-    if (continuity) k_sl_forward<T, 2, 1><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
-    else k_sl_forward<T, 2, 0><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
+    if (continuity) {
+      note_launches(1);
+      k_sl_forward<T, 2, 1><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
+    }
+    else {
+      note_launches(1);
+      k_sl_forward<T, 2, 0><<<gr, kThreads, 0, st>>>(g, m, xm, mu, out, ht);
+    }
   }
   return cudaGetLastError();
 }
@@ -211,13 +229,28 @@ cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T
 template <typename T>
 cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const T* xp, const T* mu, T* out,
                               T ht, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.dim == 3) return launch_sl_tile(g, 1, continuity, lam, xp, mu, out, ht, st);
+  }
   const unsigned gr = grid_for(g.nvox);
   if (g.dim == 3) {
-    if (continuity) k_sl_adjoint<T, 3, 1><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
-    else k_sl_adjoint<T, 3, 0><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
+    if (continuity) {
+      note_launches(1);
+      k_sl_adjoint<T, 3, 1><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
+    }
+    else {
+      note_launches(1);
+      k_sl_adjoint<T, 3, 0><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
+    }
   } else {
-    if (continuity) k_sl_adjoint<T, 2, 1><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
-    else k_sl_adjoint<T, 2, 0><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
+    if (continuity) {
+      note_launches(1);
+      k_sl_adjoint<T, 2, 1><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
+    }
+    else {
+      note_launches(1);
+      k_sl_adjoint<T, 2, 0><<<gr, kThreads, 0, st>>>(g, lam, xp, mu, out, ht);
+    }
   }
   return cudaGetLastError();
 }

@@ -107,24 +107,31 @@ k_spectral(Grid g, SpecArgs a, cx<T>* __restrict__ x, cx<T>* __restrict__ v) {
   }
 }
 
+// sum over the half spectrum of w(k) |k|^{2s} |v^_c(k)|^2 (w = 1 on the k2 = 0 and Nyquist planes,
+// 2 elsewhere). Terms are formed in the element type; each thread accumulates them in a compensated
+// (double-float for FP32) sum, CTAs combine in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_reg_sum(Grid g, int s, const cx<T>* __restrict__ vh, double* __restrict__ partial) {
   const long long nh = g.nhalf;
-  double acc = 0.0;
+  T hi = T(0), lo = T(0);
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nh;
        idx += (long long)gridDim.x * blockDim.x) {
-    const KVec<double> kv = kvec_of<double>(g, idx);
+    const KVec<T> kv = kvec_of<T>(g, idx);
     const int i2 = (int)(idx % g.n2h);
-    const double w = (i2 == 0 || 2 * i2 == g.n[2]) ? 1.0 : 2.0;
-    const double L = symbol_L<double>(kv, s);
-    double e = 0.0;
+    const T w = (i2 == 0 || 2 * i2 == g.n[2]) ? T(1) : T(2);
+    T e = T(0);
     for (int c = 0; c < g.dim; ++c) {
       const cx<T> z = vh[c * nh + idx];
-      e += (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+      e += z.x * z.x + z.y * z.y;
     }
-    acc += w * L * e;
+    const T term = w * symbol_L<T>(kv, s) * e;
+    const T t = hi + term;  // two-sum
+    const T bb = t - hi;
+    lo += (hi - (t - bb)) + (term - bb);
+    hi = t;
   }
+  double acc = (double)hi + (double)lo;
   __shared__ double red[kThreads / 32];
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -142,12 +149,14 @@ template <typename T>
 cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cx<T>* v, cudaStream_t st) {
   long long blocks = (g.nhalf + kThreads - 1) / kThreads;
   if (blocks > 152 * 8) blocks = 152 * 8;
+  note_launches(1);
   k_spectral<T><<<(unsigned)blocks, kThreads, 0, st>>>(g, a, x, v);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partial, cudaStream_t st) {
+  note_launches(1);
   k_reg_sum<T><<<kRedBlocks, kThreads, 0, st>>>(g, s, vh, partial);
   return cudaGetLastError();
 }

@@ -106,34 +106,57 @@ def eval_fourier_at(field_grid, points):
 def gaussian_mixture(n, centers, inv_covs, weights, radius):
     """Sum of periodic Gaussians w_i * exp(-0.5 (x-c_i)^T S_i (x-c_i)) on the grid.
 
-    Distances use the periodic minimum image; each Gaussian is evaluated in a box of
-    half-width `radius` (physical units) around its centre, which must cover its support.
+    Distances use the periodic minimum image; Gaussian i is evaluated in a box of half-width
+    radius[i] (physical units; a scalar applies to all) around its centre, covering its support.
+    Boxes are accumulated into a padded array that is folded back periodically at the end.
     """
     n = tuple(int(x) for x in n)
     d = len(n)
     h = spacing(n)
-    out = np.zeros(n)
-    for c, S, w in zip(centers, inv_covs, weights):
-        idx, off = [], []
+    radii = np.broadcast_to(np.asarray(radius, dtype=float), (len(centers),))
+    cells = [[min(int(np.ceil(r / h[a])), n[a]) for a in range(d)] for r in radii]
+    pad = [max([c[a] for c in cells] + [0]) + 1 for a in range(d)]
+    acc = np.zeros(tuple(n[a] + 2 * pad[a] for a in range(d)))
+    for c, S, w, rc in zip(centers, inv_covs, weights, cells):
+        offs, sl = [], []
         for a in range(d):
-            r = int(np.ceil(radius / h[a]))
-            if 2 * r + 1 >= n[a]:
-                ii = np.arange(n[a])
-            else:
-                i0 = int(np.floor(c[a] / h[a]))
-                ii = np.arange(i0 - r, i0 + r + 2) % n[a]
-            dx = ii * h[a] - c[a]
+            length = min(2 * rc[a] + 2, n[a])
+            start = int(np.floor(c[a] / h[a])) - rc[a]
+            j = np.arange(start, start + length)
+            dx = j * h[a] - c[a]
             dx = (dx + np.pi) % TWO_PI - np.pi
-            idx.append(ii)
-            off.append(dx)
-        grids = np.meshgrid(*off, indexing="ij")
-        q = np.zeros(grids[0].shape)
+            shape = [1] * d
+            shape[a] = length
+            offs.append(dx.reshape(shape))
+            sl.append(slice(start + pad[a], start + pad[a] + length))
+        q = 0.0
         for a in range(d):
-            for b in range(d):
+            q = q + S[a, a] * offs[a] * offs[a]
+            for b in range(a + 1, d):
                 if S[a, b] != 0.0:
-                    q += S[a, b] * grids[a] * grids[b]
-        out[np.ix_(*idx)] += w * np.exp(-0.5 * q)
-    return out
+                    q = q + 2.0 * S[a, b] * offs[a] * offs[b]
+        acc[tuple(sl)] += w * np.exp(-0.5 * q)
+    # fold the padding back onto the periodic grid, one axis at a time
+    for a in range(d):
+        core = [slice(None)] * d
+        lo = [slice(None)] * d
+        hi = [slice(None)] * d
+        p, m = pad[a], n[a]
+        core[a] = slice(p, p + m)
+        out = acc[tuple(core)].copy()
+        lo[a] = slice(0, p)
+        hi[a] = slice(p + m, 2 * p + m)
+        low, high = acc[tuple(lo)], acc[tuple(hi)]
+        for k in range(p):  # wrap index k - p -> k - p + m, and p + m + k -> k
+            dst = [slice(None)] * d
+            src = [slice(None)] * d
+            dst[a] = (k - p) % m
+            src[a] = k
+            out[tuple(dst)] += low[tuple(src)]
+            dst[a] = k % m
+            out[tuple(dst)] += high[tuple(src)]
+        acc = out
+    return acc
 
 
 def _random_rotation(d, rng):
@@ -174,7 +197,7 @@ def blob_image_pair(n, v_true, count, sigma_vox, rng, amplitude_sign=False, norm
     amps = rng.standard_normal(count) if amplitude_sign else np.ones(count)
     disp = np.stack([eval_fourier_at(v_true[a], centers) for a in range(d)], axis=1)
     inv = [np.eye(d) / (s * s) for s in sig]
-    rad = 5.0 * sig.max()
+    rad = 5.0 * sig
     m0 = gaussian_mixture(n, centers, inv, amps, rad)
     m1 = gaussian_mixture(n, (centers + disp) % TWO_PI, inv, amps, rad)
     if normalize:
@@ -198,14 +221,13 @@ def density_pair(n, v_true, count, sigma_vox, rng, floor=1e-3):
     centers = rng.uniform(0.0, TWO_PI, size=(count, d))
     weights = rng.uniform(0.5, 1.0, size=count)
     inv = []
-    smax = 0.0
+    rad = []
     for _ in range(count):
         s = rng.uniform(sigma_vox[0], sigma_vox[1], size=d) * hmin
-        smax = max(smax, s.max())
+        rad.append(4.5 * s.max())
         r = _random_rotation(d, rng)
         inv.append(r @ np.diag(1.0 / (s * s)) @ r.T)
     disp = np.stack([eval_fourier_at(v_true[a], centers) for a in range(d)], axis=1)
-    rad = 4.5 * smax
     p0 = gaussian_mixture(n, centers, inv, weights, rad)
     p1 = gaussian_mixture(n, (centers + disp) % TWO_PI, inv, weights, rad)
     cell = float(np.prod(h))

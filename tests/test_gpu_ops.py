@@ -177,3 +177,29 @@ def test_dots_and_lsq(prec):
     M = np.array([[gi @ gj for gj in gw] for gi in gw])
     beta = ga.ga_op_lsq(P.ctx, c, a, M)
     np.testing.assert_allclose(beta, ngmres_lsq(gq, gw), rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("model", ["advection", "continuity"])
+@pytest.mark.parametrize("vox,kmax", [(14.0, 3), (3.0, 9)])
+def test_steps_beyond_halo_and_rough_velocity(prec, model, vox, kmax):
+    """Departure points far outside the staged halo (about 7 cells per step) and rough velocities
+    whose columns do not share integer offsets take the slow paths of the tiled FP32 kernel."""
+    import paper_2510_08782_gb300 as ga
+    from synth.inputs import smooth_velocity
+
+    shape = (24, 40, 36)
+    nt = 2
+    P, m0, _, _ = _problem(shape, prec, model=model, nt=nt)
+    v = quantise(smooth_velocity(shape, kmax, vox, np.random.default_rng(12)), prec)
+    states = empty((nt + 1,) + shape, prec)
+    ga.ga_op_forward(P.ctx, P.dtype, to_dev(v, prec), states)
+    mu = osp.div(v)
+    ref = forward_states(model, m0, v, nt, mu=mu)
+    for j in range(nt + 1):
+        assert rel_l2(host(states)[j], ref[j]) < TOL[prec], j
+    lams = empty((nt + 1,) + shape, prec)
+    ga.ga_op_adjoint(P.ctx, P.dtype, to_dev(v, prec), to_dev(m0, prec), lams)
+    lref = adjoint_states(model, m0, v, nt, mu=mu)
+    for j in range(nt + 1):
+        assert rel_l2(host(lams)[j], lref[j]) < TOL[prec], j
