@@ -13,6 +13,7 @@
 // transforms of the other axes cancel), so d/dx_c costs one pass, not a 3D FFT.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <type_traits>
 
 #include "fft_core.cuh"
@@ -88,40 +89,116 @@ template <typename T> __device__ __forceinline__ void load_tw(cx<T>* tw, const c
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
 }
 
+// ---- asynchronous copies into shared memory ------------------------------------------------
+__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc));
+}
+template <typename T> __device__ __forceinline__ void cpa_elem(T* sdst, const T* gsrc) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc));
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Copy `count` contiguous elements (16-byte chunks when vec) from global to shared memory.
+template <typename T>
+__device__ __forceinline__ void stage_contig(T* dst, const T* src, int count, bool vec) {
+  constexpr int per = 16 / sizeof(T);
+  if (vec) {
+    for (int c = threadIdx.x; c < count / per; c += blockDim.x) cpa16(dst + c * per, src + c * per);
+  } else {
+    for (int e = threadIdx.x; e < count; e += blockDim.x) cpa_elem<T>(dst + e, src + e);
+  }
+}
+
+// Copy W columns x [0, W) of L strided rows (row j at src + j * S) into dst[j * W + x]; columns at or
+// beyond `valid` are not copied (the caller never reads them).
+template <typename T>
+__device__ __forceinline__ void stage_rows(T* dst, const T* src, int L, long long S, int W, int valid, bool vec) {
+  constexpr int per = 16 / sizeof(T);
+  if (vec) {  // W % per == 0, valid == W, 16-byte aligned rows
+    const int cpr = W / per;
+    for (int c = threadIdx.x; c < L * cpr; c += blockDim.x) {
+      const int j = c / cpr, k = c - j * cpr;
+      cpa16(dst + j * W + k * per, src + j * S + k * per);
+    }
+  } else {
+    for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
+      const int j = e / W, x = e - j * W;
+      if (x < valid) cpa_elem<T>(dst + e, src + j * S + x);
+    }
+  }
+}
+
+// Shared-memory layout of the derivative kernels: twiddles, two complex work buffers of B pencils
+// (the raw input block aliases the second), the raw multiplier block and the raw accumulator block.
+template <typename T> struct DerivSmem {
+  cx<T>* tw;
+  cx<T>* a;
+  cx<T>* b;
+  T* raw;
+  T* mult;
+  T* acc;
+  // regions are padded to an even number of complex entries so every region starts 16-byte aligned
+  __device__ DerivSmem(unsigned char* base, int L, int B, int ld) {
+    const size_t twn = ((size_t)L + 1) & ~(size_t)1, bufn = ((size_t)B * ld + 1) & ~(size_t)1;
+    tw = reinterpret_cast<cx<T>*>(base);
+    a = tw + twn;
+    b = a + bufn;
+    raw = reinterpret_cast<T*>(b);
+    mult = reinterpret_cast<T*>(b + bufn);
+    acc = mult + 2 * (size_t)B * L;
+  }
+};
+
 // ---- derivative along the contiguous axis (rows) --------------------------------------------
+// Rows row0 .. row0 + 2B - 1 are one contiguous block: staged raw, then paired (2p, 2p+1) into
+// complex pencils.
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
-             int accumulate, long long rows, int L, int B, int ld, FftPlan plan,
-             const cx<T>* __restrict__ twg) {
+             int accumulate, long long rows, int Lr, int B, int ld, FftPlan plan,
+             const cx<T>* __restrict__ twg, int vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* a = tw + L;
-  cx<T>* b = a + B * ld;
-  load_tw<T>(tw, twg, L);
+  const int L = NC > 0 ? NC : Lr;
+  DerivSmem<T> sm(smem_raw, L, B, ld);
   const long long row0 = (long long)blockIdx.x * 2 * B;
-  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
-    const int rr = idx / L, j = idx - rr * L;
-    const long long row = row0 + rr;
-    const T val = row < rows ? f[row * L + j] : T(0);
-    reinterpret_cast<T*>(&a[(rr >> 1) * ld + j])[rr & 1] = val;
+  const int nrows = (int)((rows - row0) < 2 * B ? (rows - row0) : 2 * B);
+  const bool full = nrows == 2 * B && vec;
+  stage_contig<T>(sm.raw, f + row0 * L, nrows * L, full);
+  cpa_commit();
+  if (mult) stage_contig<T>(sm.mult, mult + row0 * L, nrows * L, full);
+  if (accumulate) stage_contig<T>(sm.acc, out + row0 * L, nrows * L, full);
+  cpa_commit();
+  load_tw<T>(sm.tw, twg, L);
+  cpa_wait<1>();
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+    const int p = idx / L, j = idx - p * L;
+    const T va = (2 * p < nrows) ? sm.raw[(2 * p) * L + j] : T(0);
+    const T vb = (2 * p + 1 < nrows) ? sm.raw[(2 * p + 1) * L + j] : T(0);
+    sm.a[p * ld + j] = mk<T>(va, vb);
   }
   __syncthreads();
-  cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
-  cx<T>* o = (r == a) ? b : a;
+  cx<T>* r = run_fft<T, NC>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+  cx<T>* o = (r == sm.a) ? sm.b : sm.a;
   mult_ik_conj<T>(r, B, L, ld);
-  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, tw);
+  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, sm.tw);
+  cpa_wait<0>();
+  __syncthreads();
   const T inv = T(1) / T(L);
-  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < nrows * L; idx += blockDim.x) {
     const int rr = idx / L, j = idx - rr * L;
-    const long long row = row0 + rr;
-    if (row >= rows) continue;
     const cx<T> z = r2[(rr >> 1) * ld + j];
-    const T d = (rr & 1) ? -z.y * inv : z.x * inv;
-    const long long oi = row * L + j;
-    T val = coef * d;
-    if (mult) val *= mult[oi];
-    out[oi] = accumulate ? out[oi] + val : val;
+    T val = coef * ((rr & 1) ? -z.y * inv : z.x * inv);
+    if (mult) val *= sm.mult[idx];
+    if (accumulate) val += sm.acc[idx];
+    out[row0 * L + idx] = val;
   }
 }
 
@@ -129,36 +206,46 @@ k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
-             int accumulate, int L, long long S, long long outer_stride, int nx, int B, int ld,
-             FftPlan plan, const cx<T>* __restrict__ twg) {
+             int accumulate, int Lr, long long S, long long outer_stride, int nx, int B, int ld,
+             FftPlan plan, const cx<T>* __restrict__ twg, int vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* a = tw + L;
-  cx<T>* b = a + B * ld;
-  load_tw<T>(tw, twg, L);
-  const int x0 = blockIdx.x * 2 * B;
-  const long long base = (long long)blockIdx.y * outer_stride + x0;
+  const int L = NC > 0 ? NC : Lr;
+  DerivSmem<T> sm(smem_raw, L, B, ld);
   const int W = 2 * B;
-  for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
-    const int j = idx / W, xx = idx - j * W;
-    const T val = (x0 + xx < nx) ? f[base + j * S + xx] : T(0);
-    reinterpret_cast<T*>(&a[(xx >> 1) * ld + j])[xx & 1] = val;
+  const int x0 = blockIdx.x * W;
+  const long long base = (long long)blockIdx.y * outer_stride + x0;
+  const int valid = (nx - x0) < W ? (nx - x0) : W;
+  const bool v16 = vec && valid == W;
+  stage_rows<T>(sm.raw, f + base, L, S, W, valid, v16);
+  cpa_commit();
+  if (mult) stage_rows<T>(sm.mult, mult + base, L, S, W, valid, v16);
+  if (accumulate) stage_rows<T>(sm.acc, out + base, L, S, W, valid, v16);
+  cpa_commit();
+  load_tw<T>(sm.tw, twg, L);
+  cpa_wait<1>();
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+    const int j = idx / B, p = idx - j * B;
+    const T va = (2 * p < valid) ? sm.raw[j * W + 2 * p] : T(0);
+    const T vb = (2 * p + 1 < valid) ? sm.raw[j * W + 2 * p + 1] : T(0);
+    sm.a[p * ld + j] = mk<T>(va, vb);
   }
   __syncthreads();
-  cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
-  cx<T>* o = (r == a) ? b : a;
+  cx<T>* r = run_fft<T, NC>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+  cx<T>* o = (r == sm.a) ? sm.b : sm.a;
   mult_ik_conj<T>(r, B, L, ld);
-  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, tw);
+  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, sm.tw);
+  cpa_wait<0>();
+  __syncthreads();
   const T inv = T(1) / T(L);
   for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
     const int j = idx / W, xx = idx - j * W;
-    if (x0 + xx >= nx) continue;
+    if (xx >= valid) continue;
     const cx<T> z = r2[(xx >> 1) * ld + j];
-    const T d = (xx & 1) ? -z.y * inv : z.x * inv;
-    const long long oi = base + j * S + xx;
-    T val = coef * d;
-    if (mult) val *= mult[oi];
-    out[oi] = accumulate ? out[oi] + val : val;
+    T val = coef * ((xx & 1) ? -z.y * inv : z.x * inv);
+    if (mult) val *= sm.mult[idx];
+    if (accumulate) val += sm.acc[idx];
+    out[base + j * S + xx] = val;
   }
 }
 
@@ -296,6 +383,19 @@ template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
+// pencils per CTA of the derivative kernels: 2048 complex fp32 (1024 fp64) values per buffer
+template <typename T> int deriv_batch(int L) {
+  const int target = sizeof(T) == 4 ? 2048 : 1024;
+  int B = target / L;
+  return B < 1 ? 1 : B;
+}
+template <typename T> size_t deriv_smem_bytes(int L, int B) {
+  // twiddles + two complex buffers (each padded to an even count) + raw multiplier and accumulator
+  // blocks (2B x L reals each)
+  const size_t twn = ((size_t)L + 1) & ~(size_t)1, bufn = ((size_t)B * lead_dim(L) + 1) & ~(size_t)1;
+  return sizeof(cx<T>) * (twn + 2 * bufn) + 2 * sizeof(T) * 2 * (size_t)B * L;
+}
+
 template <typename T>
 cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult,
                          T* out, T coef, bool accumulate, cudaStream_t st) {
@@ -304,27 +404,31 @@ cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const 
     if (accumulate) return cudaSuccess;
     return cudaMemsetAsync(out, 0, sizeof(T) * g.nvox, st);
   }
-  int B = batch_for<T>(L);
+  int B = deriv_batch<T>(L);
   const int ld = lead_dim(L);
+  const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const bool ptrs16 = al(f) && al(out) && (!mult || al(mult));
+  constexpr int per = 16 / sizeof(T);
   if (axis == 2) {
     const long long rows = (long long)g.n[0] * g.n[1];
     const long long pairs = (rows + 1) / 2;
     if (B > pairs) B = (int)pairs;
-    const size_t sm = smem_bytes<T>(L, B);
+    const size_t sm = deriv_smem_bytes<T>(L, B);
     const long long grid = (rows + 2LL * B - 1) / (2LL * B);
+    const int vec = (ptrs16 && (L % per) == 0) ? 1 : 0;
     return with_nc<T>(L, [&](auto nc) {
       constexpr int NC = decltype(nc)::value;
       cudaError_t e = allow_smem(k_deriv_rows<T, NC>, sm);
       if (e != cudaSuccess) return e;
       note_launches(1);
       k_deriv_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, rows,
-                                                                 L, B, ld, ft.plan[2], ft.tw[2]);
+                                                                 L, B, ld, ft.plan[2], ft.tw[2], vec);
       return cudaGetLastError();
     });
   }
   const int nx = g.n[2];
   if (2 * B > nx) B = (nx + 1) / 2;
-  const size_t sm = smem_bytes<T>(L, B);
+  const size_t sm = deriv_smem_bytes<T>(L, B);
   long long S, outer_stride;
   int outer;
   if (axis == 1) {
@@ -336,6 +440,8 @@ cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const 
     outer = g.n[1];
     outer_stride = nx;
   }
+  // 16-byte chunks need whole chunks per tile row and 16-byte aligned row starts
+  const int vec = (ptrs16 && (2 * B) % per == 0 && (nx % per) == 0) ? 1 : 0;
   dim3 grid((nx + 2 * B - 1) / (2 * B), outer);
   return with_nc<T>(L, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
@@ -343,7 +449,7 @@ cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const 
     if (e != cudaSuccess) return e;
     note_launches(1);
     k_deriv_cols<T, NC><<<grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, L, S, outer_stride,
-                                                     nx, B, ld, ft.plan[axis], ft.tw[axis]);
+                                                     nx, B, ld, ft.plan[axis], ft.tw[axis], vec);
     return cudaGetLastError();
   });
 }
