@@ -83,16 +83,50 @@ template <typename T, typename C> GA_HD void dft8(C* a) {
   a[7] = csub(e[3], o3);
 }
 
+// 16-point DFT in registers as 4 x 4: inner DFT4s over n1 (stride 4), twiddles W16^(n2 k1), outer
+// DFT4s over n2; output index k1 + 4 k2.
+#define GA_C1_16 0.92387953251128675613 /* cos(pi / 8) */
+#define GA_S1_16 0.38268343236508977173 /* sin(pi / 8) */
+template <typename T, typename C> GA_HD void dft16(C* a) {
+  C y[4][4];
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C t[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
+    dft4(t);
+    for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = t[k1];
+  }
+  const T c = T(GA_C1_16), s = T(GA_S1_16), r = T(GA_SQRT1_2);
+  // W16^m = exp(-2 pi i m / 16) for m = n2 k1
+  y[1][1] = cmul(y[1][1], mk<T>(c, -s));
+  y[1][2] = cmul(y[1][2], mk<T>(r, -r));
+  y[1][3] = cmul(y[1][3], mk<T>(s, -c));
+  y[2][1] = cmul(y[2][1], mk<T>(r, -r));
+  y[2][2] = cmul_negi(y[2][2]);
+  y[2][3] = cmul(y[2][3], mk<T>(-r, -r));
+  y[3][1] = cmul(y[3][1], mk<T>(s, -c));
+  y[3][2] = cmul(y[3][2], mk<T>(-r, -r));
+  y[3][3] = cmul(y[3][3], mk<T>(-c, s));
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+    dft4(t);
+    for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[k2];
+  }
+}
+
+// Shared-memory position of pencil element i: with PS > 0 one padding entry is inserted after every
+// 2^PS entries, which makes the power-of-two strides of the Stockham stages odd and so free of
+// bank conflicts for 8-byte (complex FP32) accesses.
+template <int PS> GA_HD int fpad(int i) { return PS > 0 ? i + (i >> PS) : i; }
+
 // One butterfly of one Stockham stage. `in`/`out` point at the start of the pencil.
-template <typename T>
+template <typename T, int PS = 0>
 GA_HD void stockham_butterfly(const cx<T>* in, cx<T>* out, int j, int N, int R, int Ns,
                               const cx<T>* tw) {
   const int M = N / R;
   const int k = j % Ns;
   const int tstep = k * (N / (Ns * R));
   cx<T> v[8];
-  v[0] = in[j];
-  for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * M], tw[r * tstep]);
+  v[0] = in[fpad<PS>(j)];
+  for (int r = 1; r < R; ++r) v[r] = cmul(in[fpad<PS>(j + r * M)], tw[r * tstep]);
   switch (R) {
     case 2: dft2(v); break;
     case 3: dft3<T>(v); break;
@@ -101,7 +135,7 @@ GA_HD void stockham_butterfly(const cx<T>* in, cx<T>* out, int j, int N, int R, 
     default: dft8<T>(v); break;
   }
   const int base = (j - k) * R + k;
-  for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+  for (int r = 0; r < R; ++r) out[fpad<PS>(base + r * Ns)] = v[r];
 }
 
 // Compile-time variant of one stage for a fixed length N, radix R and span Ns: every index
@@ -109,27 +143,34 @@ GA_HD void stockham_butterfly(const cx<T>* in, cx<T>* out, int j, int N, int R, 
 #if defined(__CUDACC__)
 __host__ __device__
 #endif
-constexpr int ct_next_radix(int rem) {
-  return rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : (rem % 3 == 0 ? 3 : 5)));
+constexpr int ct_next_radix(int rem, int maxr = 16) {
+  return (maxr >= 16 && rem % 16 == 0) ? 16
+                                       : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : (rem % 3 == 0 ? 3 : 5))));
 }
 
-template <typename T, int N, int R, int Ns>
+template <typename T, int N, int R, int Ns, int PS = 0>
 GA_HD void stockham_butterfly_ct(const cx<T>* in, cx<T>* out, int j, const cx<T>* tw) {
   constexpr int M = N / R;
   const int k = j % Ns;
   const int tstep = k * (N / (Ns * R));
   cx<T> v[R];
-  v[0] = in[j];
+  v[0] = in[fpad<PS>(j)];
+  if constexpr (Ns == 1) {  // first stage: every twiddle is 1
 #pragma unroll
-  for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * M], tw[r * tstep]);
+    for (int r = 1; r < R; ++r) v[r] = in[fpad<PS>(j + r * M)];
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(in[fpad<PS>(j + r * M)], tw[r * tstep]);
+  }
   if constexpr (R == 2) dft2(v);
   else if constexpr (R == 3) dft3<T>(v);
   else if constexpr (R == 4) dft4(v);
   else if constexpr (R == 5) dft5<T>(v);
+  else if constexpr (R == 16) dft16<T>(v);
   else dft8<T>(v);
   const int base = (j - k) * R + k;
 #pragma unroll
-  for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+  for (int r = 0; r < R; ++r) out[fpad<PS>(base + r * Ns)] = v[r];
 }
 
 // Host: factor N into radices (8s first for powers of two, then 4/2, 3, 5). Returns false if N

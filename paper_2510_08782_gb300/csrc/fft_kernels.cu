@@ -23,31 +23,35 @@ namespace ga {
 
 namespace {
 
-// Compile-time stage sequence for a fixed length N (radices from ct_next_radix).
-template <typename T, int N, int Ns> struct CtStages {
+// Pencil element i of a work buffer lives at fpad<PS>(i) (one padding slot every 16 entries).
+constexpr int PS = 4;
+__device__ __forceinline__ int pd(int i) { return fpad<PS>(i); }
+
+// Compile-time stage sequence for a fixed length N (radices from ct_next_radix, at most MAXR).
+template <typename T, int N, int Ns, int MAXR> struct CtStages {
   __device__ __forceinline__ static cx<T>* run(cx<T>* a, cx<T>* b, int B, int ld, const cx<T>* tw) {
     if constexpr (Ns >= N) {
       return a;
     } else {
-      constexpr int R = ct_next_radix(N / Ns);
+      constexpr int R = ct_next_radix(N / Ns, MAXR);
       constexpr int M = N / R;
       const int total = B * M;
       for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int p = t / M;
         const int j = t - p * M;
-        stockham_butterfly_ct<T, N, R, Ns>(a + p * ld, b + p * ld, j, tw);
+        stockham_butterfly_ct<T, N, R, Ns, PS>(a + p * ld, b + p * ld, j, tw);
       }
       __syncthreads();
-      return CtStages<T, N, Ns * R>::run(b, a, B, ld, tw);
+      return CtStages<T, N, Ns * R, MAXR>::run(b, a, B, ld, tw);
     }
   }
 };
 
-template <typename T, int NC>
+template <typename T, int NC, int MAXR = 16>
 __device__ cx<T>* run_fft(cx<T>* a, cx<T>* b, int N, int B, int ld, const FftPlan& plan,
                           const cx<T>* tw) {
   if constexpr (NC > 0) {
-    return CtStages<T, NC, 1>::run(a, b, B, ld, tw);
+    return CtStages<T, NC, 1, MAXR>::run(a, b, B, ld, tw);
   }
   int Ns = 1;
   for (int s = 0; s < plan.ns; ++s) {
@@ -57,7 +61,7 @@ __device__ cx<T>* run_fft(cx<T>* a, cx<T>* b, int N, int B, int ld, const FftPla
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int p = t / M;
       const int j = t - p * M;
-      stockham_butterfly<T>(a + p * ld, b + p * ld, j, N, R, Ns, tw);
+      stockham_butterfly<T, PS>(a + p * ld, b + p * ld, j, N, R, Ns, tw);
     }
     __syncthreads();
     cx<T>* tmp = a;
@@ -79,8 +83,8 @@ template <typename T> __device__ __forceinline__ void mult_ik_conj(cx<T>* r, int
   for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
     const int p = idx / L, j = idx - p * L;
     const T kt = ktilde<T>(j, L);
-    const cx<T> z = r[p * ld + j];
-    r[p * ld + j] = mk<T>(-kt * z.y, -kt * z.x);
+    const cx<T> z = r[p * ld + pd(j)];
+    r[p * ld + pd(j)] = mk<T>(-kt * z.y, -kt * z.x);
   }
   __syncthreads();
 }
@@ -182,19 +186,19 @@ k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
     const int p = idx / L, j = idx - p * L;
     const T va = (2 * p < nrows) ? sm.raw[(2 * p) * L + j] : T(0);
     const T vb = (2 * p + 1 < nrows) ? sm.raw[(2 * p + 1) * L + j] : T(0);
-    sm.a[p * ld + j] = mk<T>(va, vb);
+    sm.a[p * ld + pd(j)] = mk<T>(va, vb);
   }
   __syncthreads();
-  cx<T>* r = run_fft<T, NC>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+  cx<T>* r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
   cx<T>* o = (r == sm.a) ? sm.b : sm.a;
   mult_ik_conj<T>(r, B, L, ld);
-  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, sm.tw);
+  cx<T>* r2 = run_fft<T, NC, 8>(r, o, L, B, ld, plan, sm.tw);
   cpa_wait<0>();
   __syncthreads();
   const T inv = T(1) / T(L);
   for (int idx = threadIdx.x; idx < nrows * L; idx += blockDim.x) {
     const int rr = idx / L, j = idx - rr * L;
-    const cx<T> z = r2[(rr >> 1) * ld + j];
+    const cx<T> z = r2[(rr >> 1) * ld + pd(j)];
     T val = coef * ((rr & 1) ? -z.y * inv : z.x * inv);
     if (mult) val *= sm.mult[idx];
     if (accumulate) val += sm.acc[idx];
@@ -228,20 +232,20 @@ k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
     const int j = idx / B, p = idx - j * B;
     const T va = (2 * p < valid) ? sm.raw[j * W + 2 * p] : T(0);
     const T vb = (2 * p + 1 < valid) ? sm.raw[j * W + 2 * p + 1] : T(0);
-    sm.a[p * ld + j] = mk<T>(va, vb);
+    sm.a[p * ld + pd(j)] = mk<T>(va, vb);
   }
   __syncthreads();
-  cx<T>* r = run_fft<T, NC>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+  cx<T>* r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
   cx<T>* o = (r == sm.a) ? sm.b : sm.a;
   mult_ik_conj<T>(r, B, L, ld);
-  cx<T>* r2 = run_fft<T, NC>(r, o, L, B, ld, plan, sm.tw);
+  cx<T>* r2 = run_fft<T, NC, 8>(r, o, L, B, ld, plan, sm.tw);
   cpa_wait<0>();
   __syncthreads();
   const T inv = T(1) / T(L);
   for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
     const int j = idx / W, xx = idx - j * W;
     if (xx >= valid) continue;
-    const cx<T> z = r2[(xx >> 1) * ld + j];
+    const cx<T> z = r2[(xx >> 1) * ld + pd(j)];
     T val = coef * ((xx & 1) ? -z.y * inv : z.x * inv);
     if (mult) val *= sm.mult[idx];
     if (accumulate) val += sm.acc[idx];
@@ -252,98 +256,115 @@ k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
 // ---- real-to-complex FFT of row pairs ---------------------------------------------------------
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
-k_r2c_rows(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, int L, int Lh, int B,
-           int ld, FftPlan plan, const cx<T>* __restrict__ twg) {
+k_r2c_rows(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, int Lr, int Lh, int B,
+           int ld, FftPlan plan, const cx<T>* __restrict__ twg, int vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* a = tw + L;
-  cx<T>* b = a + B * ld;
-  load_tw<T>(tw, twg, L);
+  const int L = NC > 0 ? NC : Lr;
+  DerivSmem<T> sm(smem_raw, L, B, ld);
   const long long row0 = (long long)blockIdx.x * 2 * B;
-  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
-    const int rr = idx / L, j = idx - rr * L;
-    const long long row = row0 + rr;
-    const T val = row < rows ? f[row * L + j] : T(0);
-    reinterpret_cast<T*>(&a[(rr >> 1) * ld + j])[rr & 1] = val;
+  const int nrows = (int)((rows - row0) < 2 * B ? (rows - row0) : 2 * B);
+  stage_contig<T>(sm.raw, f + row0 * L, nrows * L, nrows == 2 * B && vec);
+  cpa_commit();
+  load_tw<T>(sm.tw, twg, L);
+  cpa_wait<0>();
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+    const int p = idx / L, j = idx - p * L;
+    const T va = (2 * p < nrows) ? sm.raw[(2 * p) * L + j] : T(0);
+    const T vb = (2 * p + 1 < nrows) ? sm.raw[(2 * p + 1) * L + j] : T(0);
+    sm.a[p * ld + pd(j)] = mk<T>(va, vb);
   }
   __syncthreads();
-  const cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
-  for (int idx = threadIdx.x; idx < B * Lh; idx += blockDim.x) {
-    const int p = idx / Lh, k = idx - p * Lh;
-    const cx<T> zk = r[p * ld + k];
-    const cx<T> zm = cconj(r[p * ld + (k == 0 ? 0 : L - k)]);
-    const cx<T> A = cscale(cadd(zk, zm), T(0.5));
-    const cx<T> Bv = cscale(cmul_negi(csub(zk, zm)), T(0.5));
-    const long long ra = row0 + 2 * p;
-    if (ra < rows) fh[ra * Lh + k] = A;
-    if (ra + 1 < rows) fh[(ra + 1) * Lh + k] = Bv;
+  const cx<T>* r = run_fft<T, NC>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+  for (int idx = threadIdx.x; idx < 2 * B * Lh; idx += blockDim.x) {
+    const int rr = idx / Lh, k = idx - rr * Lh;
+    if (rr >= nrows) continue;
+    const int p = rr >> 1;
+    const cx<T> zk = r[p * ld + pd(k)];
+    const cx<T> zm = cconj(r[p * ld + pd(k == 0 ? 0 : L - k)]);
+    // row 2p: A_k = (Z_k + conj Z_-k) / 2;  row 2p+1: B_k = (Z_k - conj Z_-k) / (2 i)
+    fh[(row0 + rr) * Lh + k] = (rr & 1) ? cscale(cmul_negi(csub(zk, zm)), T(0.5)) : cscale(cadd(zk, zm), T(0.5));
   }
 }
 
 // ---- complex-to-real inverse FFT of row pairs (normalised by `scale`) --------------------------
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
-k_c2r_rows(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, int L, int Lh, int B,
-           int ld, FftPlan plan, const cx<T>* __restrict__ twg, T scale) {
+k_c2r_rows(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, int Lr, int Lh, int B,
+           int ld, FftPlan plan, const cx<T>* __restrict__ twg, T scale, int vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* a = tw + L;
-  cx<T>* b = a + B * ld;
-  load_tw<T>(tw, twg, L);
+  const int L = NC > 0 ? NC : Lr;
+  DerivSmem<T> sm(smem_raw, L, B, ld);
   const long long row0 = (long long)blockIdx.x * 2 * B;
-  for (int idx = threadIdx.x; idx < 2 * B * Lh; idx += blockDim.x) {
-    const int rr = idx / Lh, k = idx - rr * Lh;
-    const long long row = row0 + rr;
-    const cx<T> val = row < rows ? fh[row * Lh + k] : mk<T>(T(0), T(0));
-    ((rr & 1) ? b : a)[(rr >> 1) * ld + k] = val;
-  }
+  const int nrows = (int)((rows - row0) < 2 * B ? (rows - row0) : 2 * B);
+  // the 2B x Lh complex block is contiguous; it is staged in the raw multiplier area
+  cx<T>* stg = reinterpret_cast<cx<T>*>(sm.mult);
+  stage_contig<T>(reinterpret_cast<T*>(stg), reinterpret_cast<const T*>(fh + row0 * Lh), 2 * nrows * Lh,
+                  nrows == 2 * B && vec);
+  cpa_commit();
+  load_tw<T>(sm.tw, twg, L);
+  cpa_wait<0>();
   __syncthreads();
   // Z_k = A_k + i B_k (k < Lh) and Z_{L-k} = conj(A_k) + i conj(B_k); store conj(Z) in `a`.
   for (int idx = threadIdx.x; idx < B * Lh; idx += blockDim.x) {
     const int p = idx / Lh, k = idx - p * Lh;
-    const cx<T> A = a[p * ld + k], Bv = b[p * ld + k];
-    const cx<T> z = mk<T>(A.x - Bv.y, A.y + Bv.x);
-    a[p * ld + k] = cconj(z);
-    if (k >= 1 && L - k >= Lh) {
-      const cx<T> zm = mk<T>(A.x + Bv.y, -A.y + Bv.x);  // conj(A) + i conj(B)
-      a[p * ld + L - k] = cconj(zm);
-    }
+    const cx<T> A = (2 * p < nrows) ? stg[(2 * p) * Lh + k] : mk<T>(T(0), T(0));
+    const cx<T> Bv = (2 * p + 1 < nrows) ? stg[(2 * p + 1) * Lh + k] : mk<T>(T(0), T(0));
+    sm.a[p * ld + pd(k)] = cconj(mk<T>(A.x - Bv.y, A.y + Bv.x));
+    if (k >= 1 && L - k >= Lh) sm.a[p * ld + pd(L - k)] = cconj(mk<T>(A.x + Bv.y, -A.y + Bv.x));
   }
   __syncthreads();
-  const cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
-  for (int idx = threadIdx.x; idx < 2 * B * L; idx += blockDim.x) {
+  const cx<T>* r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+  for (int idx = threadIdx.x; idx < nrows * L; idx += blockDim.x) {
     const int rr = idx / L, j = idx - rr * L;
-    const long long row = row0 + rr;
-    if (row >= rows) continue;
-    const cx<T> z = r[(rr >> 1) * ld + j];
-    f[row * L + j] = ((rr & 1) ? -z.y : z.x) * scale;
+    const cx<T> z = r[(rr >> 1) * ld + pd(j)];
+    f[row0 * L + idx] = ((rr & 1) ? -z.y : z.x) * scale;
   }
 }
 
 // ---- complex FFT along a strided axis of the half spectrum, in place ---------------------------
+template <typename T> __device__ __forceinline__ void cpa_cx(cx<T>* sdst, const cx<T>* gsrc) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc));
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc));
+}
+
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
-k_fft_cols(cx<T>* __restrict__ fh, int L, long long S, long long outer_stride, int nx, int B, int ld,
+k_fft_cols(cx<T>* __restrict__ fh, int Lr, long long S, long long outer_stride, int nx, int B, int ld,
            FftPlan plan, const cx<T>* __restrict__ twg, int inverse, T scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = NC > 0 ? NC : Lr;
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* a = tw + L;
-  cx<T>* b = a + B * ld;
-  load_tw<T>(tw, twg, L);
+  cx<T>* a = tw + ((L + 1) & ~1);
+  cx<T>* b = a + (((size_t)B * ld + 1) & ~(size_t)1);
   const int x0 = blockIdx.x * B;
   const long long base = (long long)blockIdx.y * outer_stride + x0;
+  const int valid = (nx - x0) < B ? (nx - x0) : B;
+  // stage the tile as b[j * B + p]
   for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
     const int j = idx / B, p = idx - j * B;
-    cx<T> z = (x0 + p < nx) ? fh[base + j * S + p] : mk<T>(T(0), T(0));
+    if (p < valid) cpa_cx<T>(b + idx, fh + base + j * S + p);
+  }
+  cpa_commit();
+  load_tw<T>(tw, twg, L);
+  cpa_wait<0>();
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+    const int j = idx / B, p = idx - j * B;
+    cx<T> z = (p < valid) ? b[idx] : mk<T>(T(0), T(0));
     if (inverse) z = cconj(z);
-    a[p * ld + j] = z;
+    a[p * ld + pd(j)] = z;
   }
   __syncthreads();
   const cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
   for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
     const int j = idx / B, p = idx - j * B;
-    if (x0 + p >= nx) continue;
-    cx<T> z = r[p * ld + j];
+    if (p >= valid) continue;
+    cx<T> z = r[p * ld + pd(j)];
     if (inverse) z = cscale(cconj(z), scale);
     fh[base + j * S + p] = z;
   }
@@ -355,9 +376,15 @@ template <typename T> int batch_for(int L) {
   int B = target / L;
   return B < 1 ? 1 : B;
 }
-inline int lead_dim(int L) { return (L % 2 == 0) ? L + 1 : L; }
+// pitch of one pencil in a work buffer: room for the padded index of element L - 1, made odd so that
+// the same element of consecutive pencils falls in different banks
+inline int lead_dim(int L) {
+  const int ld = L + (L >> PS) + 1;
+  return (ld % 2 == 0) ? ld + 1 : ld;
+}
 template <typename T> size_t smem_bytes(int L, int B) {
-  return sizeof(cx<T>) * ((size_t)L + 2 * (size_t)B * lead_dim(L));
+  const size_t twn = ((size_t)L + 1) & ~(size_t)1, bufn = ((size_t)B * lead_dim(L) + 1) & ~(size_t)1;
+  return sizeof(cx<T>) * (twn + 2 * bufn);
 }
 
 // Calls f(std::integral_constant<int, NC>) with NC = L for the FP32 lengths that have a compile-time
@@ -369,6 +396,7 @@ template <typename T, typename F> cudaError_t with_nc(int L, F&& f) {
       case 96: return f(std::integral_constant<int, 96>());
       case 128: return f(std::integral_constant<int, 128>());
       case 160: return f(std::integral_constant<int, 160>());
+      case 192: return f(std::integral_constant<int, 192>());
       case 256: return f(std::integral_constant<int, 256>());
       default: break;
     }
@@ -496,12 +524,15 @@ cudaError_t launch_r2c(const Grid& g, const FftTables<T>& ft, const T* f, cx<T>*
   const int ld = lead_dim(L);
   const size_t sm = smem_bytes<T>(L, B);
   const long long grid = (rows + 2LL * B - 1) / (2LL * B);
+  constexpr int per = 16 / sizeof(T);
+  const int vec = ((reinterpret_cast<uintptr_t>(f) & 15u) == 0 && L % per == 0) ? 1 : 0;
   cudaError_t e = with_nc<T>(L, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
     cudaError_t e2 = allow_smem(k_r2c_rows<T, NC>, sm);
     if (e2 != cudaSuccess) return e2;
     note_launches(1);
-    k_r2c_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(f, fh, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2]);
+    k_r2c_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(f, fh, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2],
+                                                             vec);
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
@@ -516,18 +547,19 @@ cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, c
   if ((e = launch_cols<T>(g, ft, 1, fh, 1, st)) != cudaSuccess) return e;
   const int L = g.n[2];
   const long long rows = (long long)g.n[0] * g.n[1];
-  int B = batch_for<T>(L);
+  int B = deriv_batch<T>(L);  // the staged half-spectrum block uses the multiplier/accumulator area
   if (B > (rows + 1) / 2) B = (int)((rows + 1) / 2);
   const int ld = lead_dim(L);
-  const size_t sm = smem_bytes<T>(L, B);
+  const size_t sm = deriv_smem_bytes<T>(L, B);
   const long long grid = (rows + 2LL * B - 1) / (2LL * B);
+  const int vec = (reinterpret_cast<uintptr_t>(fh) & 15u) == 0 ? 1 : 0;
   return with_nc<T>(L, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
     cudaError_t e2 = allow_smem(k_c2r_rows<T, NC>, sm);
     if (e2 != cudaSuccess) return e2;
     note_launches(1);
     k_c2r_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(fh, f, rows, L, g.n2h, B, ld, ft.plan[2], ft.tw[2],
-                                                             T(1) / T(L));
+                                                             T(1) / T(L), vec);
     return cudaGetLastError();
   });
 }

@@ -297,7 +297,7 @@ template <typename T> struct Engine : EngineBase {
 
   // State solve keeping only the final state; returns pointer to m(1).
   const T* forward_final(const T* v) {
-    ck(launch_departure<T>(g, v, xm, xp, (T)ht, st), "departure");
+    ck(launch_departure<T>(g, v, xm, xp, (T)ht, st, /*both=*/0), "departure");
     const T* cur = m0;
     for (int j = 0; j < nt; ++j) {
       T* dst = tmp[(j + 1) & 1];

@@ -53,9 +53,11 @@ template <typename T>
 cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partial, cudaStream_t st);
 
 // ---- semi-Lagrangian transport (sl_kernels.cu) -----------------------------------------------
-// Displacements (grid units) of the RK2 departure points X- (xm) and X+ (xp).
+// Displacements (grid units) of the RK2 departure points X- (xm) and, when both != 0, X+ (xp).
 template <typename T>
-cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cudaStream_t st);
+cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cudaStream_t st, int both = 1);
+cudaError_t launch_departure_tile(const Grid& g, const float* v, float* xm, float* xp, float ht, int both,
+                                  cudaStream_t st);
 // One state step m_{j+1} = I[m_j](X-) (continuity: with the RK2 source of -pi div v).
 template <typename T>
 cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T* xm, const T* mu,

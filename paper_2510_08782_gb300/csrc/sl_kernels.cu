@@ -188,7 +188,10 @@ inline unsigned grid_for(long long n) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cudaStream_t st) {
+cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cudaStream_t st, int both) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.dim == 3) return launch_departure_tile(g, v, xm, xp, ht, both, st);
+  }
   note_launches(1);
   if (g.dim == 3)
     k_departure<T, 3><<<grid_for(g.nvox), kThreads, 0, st>>>(g, v, xm, xp, ht);
@@ -256,7 +259,7 @@ cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const
 }
 
 #define GA_INST(T)                                                                                  \
-  template cudaError_t launch_departure<T>(const Grid&, const T*, T*, T*, T, cudaStream_t);         \
+  template cudaError_t launch_departure<T>(const Grid&, const T*, T*, T*, T, cudaStream_t, int);    \
   template cudaError_t launch_sl_forward<T>(const Grid&, int, const T*, const T*, const T*, T*, T,    \
                                             cudaStream_t);                                           \
   template cudaError_t launch_sl_adjoint<T>(const Grid&, int, const T*, const T*, const T*, T*, T,    \

@@ -1,12 +1,12 @@
 // Tiled FP32 semi-Lagrangian step for 3D grids (Sec. 2.2; same arithmetic as sl_kernels.cu).
 //
 // A CTA owns a brick of 32 x 8 x 8 voxels (x contiguous). It stages the brick plus a periodic halo
-// (4 cells below / 4 above in x, 3 / 3 in y and z) of the transported field, and of mu for the
-// two-field steps, into shared memory with 16-byte cp.async copies. Each thread owns a column of 8
-// voxels along z and interpolates them one by one: a departure point whose integer offset lies in
-// [-2, 1] on every axis reads its 64 taps from shared memory (the product field f * mu is formed
-// tap by tap); any other departure point reads the field from global memory, so every displacement
-// is handled exactly.
+// (4 cells below / 4 above in x, 3 / 3 in y and z) of the transported field into shared memory with
+// 16-byte cp.async copies (and mu for the two-field steps). Each thread owns a column of 8 voxels
+// along z and interpolates them one by one: a departure point whose integer offset lies in [-2, 1]
+// on every axis reads its 64 taps from shared memory (the product f * mu is formed tap by tap); any
+// other departure point reads the field from global memory, so every displacement is handled
+// exactly.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -202,11 +202,82 @@ k_sl_tile(const float* __restrict__ f, const float* __restrict__ mu, const float
   }
 }
 
+// RK2 departure points (displacements in cells) for 3D FP32 grids: X* = x -/+ h_t v(x), then
+// X-/+ = x -/+ (h_t / 2)(v(x) + I[v](X*)). The three velocity components of the brick + halo are
+// staged in shared memory; the three interpolants at X* share one stencil.
+__global__ void __launch_bounds__(256, 2)
+k_departure_tile(const float* __restrict__ v, float* __restrict__ xm, float* __restrict__ xp, int n0, int n1, int n2,
+                 float ht, int both, int vec) {
+  extern __shared__ __align__(16) float smem[];
+  const long long nv = (long long)n0 * n1 * n2;
+  const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
+  const BrickIdx bi = brick_of(blockIdx.x, nbx, nby);
+  for (int c = 0; c < 3; ++c) stage_async(smem + c * TILEA, v + c * nv, bi, n0, n1, n2, vec != 0);
+  cp_async_commit();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gx = bi.bx * BX + lane, gy = bi.by * BY + warp;
+  const float twopi = 6.283185307179586f;
+  const float ih[3] = {(float)n0 / twopi, (float)n1 / twopi, (float)n2 / twopi};  // 1 / h_a
+  asm volatile("cp.async.wait_all;\n" ::);
+  __syncthreads();
+  if (gx >= n2 || gy >= n1) return;
+  const int nz = min(BZ, n0 - bi.bz * BZ);
+#pragma unroll 1
+  for (int vz = 0; vz < nz; ++vz) {
+    const long long idx = ((long long)(bi.bz * BZ + vz) * n1 + gy) * n2 + gx;
+    const int center = ((vz + H + 1) * TY + warp + H + 1) * TXA + lane + XOFF;
+    float vc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vc[c] = smem[c * TILEA + center];
+#pragma unroll 1
+    for (int sg = 0; sg < (both ? 2 : 1); ++sg) {
+      const float sign = sg == 0 ? 1.f : -1.f;
+      float* o = sg == 0 ? xm : xp;
+      const float dz = -sign * ht * vc[0] * ih[0], dy = -sign * ht * vc[1] * ih[1], dx = -sign * ht * vc[2] * ih[2];
+      const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
+      if (fz >= -H && fz <= H - 1 && fy >= -H && fy <= H - 1 && fx >= -H && fx <= H - 1) {
+        float wz[4], wy[4], wx[4];
+        lagrange4(dz - fz, wz);
+        lagrange4(dy - fy, wy);
+        lagrange4(dx - fx, wx);
+        const int base = ((vz + H + (int)fz) * TY + warp + H + (int)fy) * TXA + lane + XOFF - 1 + (int)fx;
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) {  // one component at a time: the stencil weights are shared
+          const float* t = smem + k * TILEA + base;
+          float acc = 0.f;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float ay = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const float* r = t + (c * TY + b) * TXA;
+              ay += wy[b] * (wx[0] * r[0] + wx[1] * r[1] + wx[2] * r[2] + wx[3] * r[3]);
+            }
+            acc += wz[c] * ay;
+          }
+          const float vk = k == 0 ? vc[0] : (k == 1 ? vc[1] : vc[2]);
+          const float ihk = k == 0 ? ih[0] : (k == 1 ? ih[1] : ih[2]);
+          o[k * nv + idx] = -sign * 0.5f * ht * (vk + acc) * ihk;
+        }
+      } else {
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) {
+          float P, S;
+          gather_global<1>(v + k * nv, nullptr, bi.bz * BZ + vz, gy, gx, dz, dy, dx, n0, n1, n2, P, S);
+          const float vk = k == 0 ? vc[0] : (k == 1 ? vc[1] : vc[2]);
+          const float ihk = k == 0 ? ih[0] : (k == 1 ? ih[1] : ih[2]);
+          o[k * nv + idx] = -sign * 0.5f * ht * (vk + P) * ihk;
+        }
+      }
+    }
+  }
+}
+
 template <int MODE>
 cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
                         cudaStream_t st) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
-  const size_t sm = sizeof(float) * TILEA * NF;
+  const size_t sm = sizeof(float) * TILEA * NF;  // two-field steps: TILEA float2 pairs
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_sl_tile<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -224,6 +295,23 @@ cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const fl
 }
 
 }  // namespace
+
+cudaError_t launch_departure_tile(const Grid& g, const float* v, float* xm, float* xp, float ht, int both,
+                                  cudaStream_t st) {
+  const size_t sm = sizeof(float) * TILEA * 3;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_departure_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nb = ((g.n[2] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[0] + BZ - 1) / BZ);
+  const bool aligned = (reinterpret_cast<uintptr_t>(v) & 15u) == 0;
+  const int vec = (g.n[2] % 4 == 0 && g.n[2] >= TXA && g.n[1] >= TY && g.n[0] >= TZ && aligned) ? 1 : 0;
+  note_launches(1);
+  k_departure_tile<<<nb, 256, sm, st>>>(v, xm, xp, g.n[0], g.n[1], g.n[2], ht, both, vec);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sl_tile(const Grid& g, int adjoint, int continuity, const float* f, const float* disp,
                            const float* mu, float* out, float ht, cudaStream_t st) {

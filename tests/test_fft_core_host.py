@@ -20,3 +20,5 @@ def test_stockham_core_matches_direct_dft():
                                   100, 125, 128, 144, 160, 192, 243, 250, 256, 384, 512, 1000, 1024)]
         r = subprocess.run([exe, *sizes], capture_output=True, text=True)
         assert r.returncode == 0, r.stdout
+        r = subprocess.run([exe, "ct"], capture_output=True, text=True)
+        assert r.returncode == 0, r.stdout
