@@ -89,6 +89,29 @@ ga_status ga_prof_stop(ga_ctx* ctx, double* total_ms, long long* launches);
 /* Number of CUDA kernels the library has launched in this process so far (all contexts). */
 long long ga_kernel_launches(void);
 
+/* Inner products for callers that cannot allocate device memory. The paper has no counterpart:
+ * this is a convenience of the library. It computes the same FP64-accurate compensated inner
+ * products as ga_op_dots, out[i] = sum_j a[j] * b_i[j] for i < count, without a context and without
+ * calling cudaMalloc, cudaFree or any allocating routine. It is meant for programs that have handed
+ * all device memory to their own allocator or pool, and for latency-critical loops that must not
+ * pay for an allocation or the device-wide synchronisation that freeing implies.
+ *   prec    GA_PREC_FP64 (a, b_i are double) or GA_PREC_MIXED (float); products are summed in FP64.
+ *   a       device vector of len elements; b: HOST array of count device vectors of len elements.
+ *   count   1..32: the per-CTA partial sums of all count products live in one fixed device array of
+ *           32 * 608 doubles (155,648 bytes) defined in the library, which every GPU that loads the
+ *           library holds until the process exits. count > 32 returns GA_ERR_ARG with a message.
+ *   out     DEVICE array of count doubles, written in stream order.
+ *   stream  cudaStream_t (NULL = legacy default stream); the call returns without synchronising.
+ * The first call on a device looks up the device address of the fixed array (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Every call on a device shares the array and it
+ * keeps the last call's contents (each call rewrites every partial it reads, so nothing needs
+ * clearing); calls whose work overlaps on the GPU, e.g. on two streams at once, race on the array
+ * and must be serialised by the caller. Errors: GA_ERR_ARG for null pointers, len 0, an unknown
+ * precision or count outside 1..32; GA_ERR_CUDA for a launch failure; ga_last_error(NULL) holds the
+ * reason. */
+ga_status ga_dots_noalloc(int prec, const void* a, const void* const* b, int count, size_t len,
+                          double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

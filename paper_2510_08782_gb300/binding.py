@@ -91,6 +91,7 @@ _SIGS = {
     "ga_prof_start": ([_vp, _c_int], _c_int),
     "ga_prof_stop": ([_vp, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)], _c_int),
     "ga_kernel_launches": ([], ctypes.c_longlong),
+    "ga_dots_noalloc": ([_c_int, _vp, ctypes.POINTER(_vp), _c_int, ctypes.c_size_t, _vp, _vp], _c_int),
 }
 
 
@@ -307,6 +308,20 @@ def ga_op_lsq(ctx, c, a, M):
     _check(lib().ga_op_lsq(ctx, m, float(c), a.ctypes.data_as(dp), M.ctypes.data_as(dp),
                            beta.ctypes.data_as(dp)), ctx)
     return beta
+
+
+def ga_dots_noalloc(dtype, a, bs, out, stream=None):
+    """FP64-accurate inner products <a, b_i> into the device array `out` (float64, len(bs)) without
+    any device allocation; see include/ga_ops.h for who needs this and its limits (at most 32 vectors,
+    calls that overlap on the GPU race)."""
+    ptrs = _dev(dtype, a, *bs)
+    (pout,) = _dev(np.float64, out)
+    n = len(bs)
+    arr = (_vp * n)(*ptrs[1:])
+    prec = GA_PREC_FP64 if dtype == np.float64 else GA_PREC_MIXED
+    st = lib().ga_dots_noalloc(prec, ptrs[0], arr, n, int(np.prod(tuple(a.shape))), pout,
+                               _vp(stream if stream is not None else _current_stream()))
+    _check(st, None)
 
 
 def ga_prof_start(ctx, kernel_class):

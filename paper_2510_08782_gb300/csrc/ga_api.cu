@@ -615,6 +615,12 @@ template <typename T> void stage_out(Engine<T>& e, void* p, const T* src, long l
 
 }  // namespace
 
+static thread_local std::string g_setup_err;
+
+namespace ga {
+void set_global_error(const char* msg) { g_setup_err = msg ? msg : ""; }
+}  // namespace ga
+
 extern "C" {
 
 const char* ga_status_str(ga_status s) {
@@ -631,7 +637,6 @@ const char* ga_status_str(ga_status s) {
   return "GA_ERR_UNKNOWN";
 }
 
-static thread_local std::string g_setup_err;
 
 const char* ga_last_error(const ga_ctx* ctx) {
   if (ctx) return ctx->err.c_str();

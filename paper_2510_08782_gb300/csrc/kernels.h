@@ -17,6 +17,8 @@ template <typename T> struct PtrList { const T* p[16]; };
 
 // Counts kernel launches issued by the library (process-wide).
 void note_launches(int n);
+// Message returned by ga_last_error(NULL) on this thread (calls that have no context).
+void set_global_error(const char* msg);
 
 template <typename T> struct FftTables {
   FftPlan plan[3];
