@@ -340,11 +340,21 @@ template <typename T> struct Engine : EngineBase {
   }
 
   // obj(v): one state solve. Results: dres[0] = sum (m(1) - m1)^2, dres[1] = regulariser sum.
-  double objective(const T* v, double* mismatch = nullptr) {
+  // With keep = true the state solve stores its trajectory (and v^, mu, X-) so that an immediately
+  // following gradient(v) on the same, unmodified buffer reuses them instead of solving again.
+  double objective(const T* v, double* mismatch = nullptr, bool keep = false) {
+    fwd_cache = nullptr;
     ck(cudaEventRecord(ev[0], st), "event");
     prologue(v, 1);
-    if (needs_mu_forward()) compute_mu(v);
-    const T* mT = forward_final(v);
+    if (needs_mu_forward() || keep) compute_mu(v);
+    const T* mT;
+    if (keep) {
+      ck(launch_departure<T>(g, v, xm, xp, (T)ht, st, /*both=*/0), "departure");
+      forward_all();
+      mT = slot(nt);
+    } else {
+      mT = forward_final(v);
+    }
     ck(launch_mismatch<T>(mT, m1, nullptr, nv, dpart, dres, st), "mismatch");
     ck(cudaEventRecord(ev[1], st), "event");
     read_results(2);
@@ -355,8 +365,10 @@ template <typename T> struct Engine : EngineBase {
     ctx->stats.pde_solves += 1;
     const double m = 0.5 * hd * hres[0];
     if (mismatch) *mismatch = m;
+    if (keep) fwd_cache = v;
     return m + reg_value(hres[1]);
   }
+  const T* fwd_cache = nullptr;  // v whose trajectory, v^, mu and X- are current (see objective)
 
   // Body force b (not projected) from the adjoint started at lam_init (lam_init may be lam[0]).
   // Requires departure points, mu and the forward states.
@@ -385,10 +397,17 @@ template <typename T> struct Engine : EngineBase {
   // Reduced gradient; writes g (vl) and, when s_out != nullptr, s = -(alpha L)^{-1} (P) g.
   double gradient(const T* v, T* gout, T* s_out, double* mismatch = nullptr) {
     ck(cudaEventRecord(ev[0], st), "event");
-    prologue(v, 1);
-    compute_mu(v);
-    ck(launch_departure<T>(g, v, xm, xp, (T)ht, st), "departure");
-    forward_all();
+    const bool reuse = fwd_cache == v;  // trajectory of the last objective(v, .., keep) call
+    fwd_cache = nullptr;
+    if (reuse) {
+      // v^, its regulariser sum, mu, X- and the stored states are those of v: only X+ is missing
+      ck(launch_departure<T>(g, v, xp, xm, (T)(-ht), st, /*both=*/0), "departure");
+    } else {
+      prologue(v, 1);
+      compute_mu(v);
+      ck(launch_departure<T>(g, v, xm, xp, (T)ht, st), "departure");
+      forward_all();
+    }
     ck(launch_mismatch<T>(slot(nt), m1, lam[0], nv, dpart, dres, st), "mismatch");
     body_force(lam[0]);
     for (int c = 0; c < dim; ++c) r2c(body + c * nv, bh + c * g.nhalf);
@@ -404,7 +423,7 @@ template <typename T> struct Engine : EngineBase {
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
     ctx->stats.t_grad_ms += ms;
     ctx->stats.grad_evals += 1;
-    ctx->stats.pde_solves += 2;
+    ctx->stats.pde_solves += reuse ? 1 : 2;
     const double m = 0.5 * hd * hres[0];
     if (mismatch) *mismatch = m;
     const double val = m + reg_value(hres[1]);
@@ -509,7 +528,7 @@ template <typename T> struct Engine : EngineBase {
     bool ok = false;
     for (int it = 0; it <= o.max_backtracks; ++it) {
       ck(launch_axpy<T>(q, v, S, rho, vl, st), "axpy");
-      Jq = objective(q);
+      Jq = objective(q, nullptr, /*keep=*/true);
       stt.ls_trials += 1;
       if (Jq < J + o.armijo_c * rho * gs) {
         rho_mem = (it == 0) ? 2.0 * rho : rho;
@@ -593,8 +612,14 @@ template <typename F> ga_status guard(ga_ctx* c, F&& f) {
 template <typename F> ga_status dispatch(ga_ctx* c, F&& fn) {
   if (!c) return GA_ERR_ARG;
   return guard(c, [&] {
-    if (c->ef) fn(*c->ef);
-    else fn(*c->ed);
+    // the reuse of a line-search state solve never spans two calls of the C ABI
+    if (c->ef) {
+      c->ef->fwd_cache = nullptr;
+      fn(*c->ef);
+    } else {
+      c->ed->fwd_cache = nullptr;
+      fn(*c->ed);
+    }
   });
 }
 
