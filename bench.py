@@ -45,6 +45,11 @@ CPU_SAMPLE_N = 48  # oracle sample grid (same recipe), scaled to 256^3 by voxel 
 # kernel classes timed with events inside the library (ga_prof_start)
 PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ = 0, 1, 2, 3
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sl_tile<1> launch from an ncu
+# capture of this benchmark at 192^3 (profiles/k_sl_tile_state_cont192.md: 143.4 MB + 17.3 MB),
+# scaled to n^3 by the voxel count. Valid for the kernel as captured; set to None when it changes.
+SL_FWD_TRAFFIC_192 = 160.7e6
+
 
 def peaks():
     try:
@@ -164,6 +169,8 @@ def main():
     ap.add_argument("--no-tts", action="store_true")
     ap.add_argument("--prof-class", type=int, default=PROF_SL_FWD)
     ap.add_argument("--grid", type=int, default=N, help="grid size (default 256; smaller only for smoke runs)")
+    ap.add_argument("--fp64-tts", action="store_true",
+                    help="also time the same GA-NGMRES solve with the FP64 GPU path (slow: FP64 is ALU-bound on GB300)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -247,8 +254,13 @@ def main():
     per_launch_ms = prof_ms / max(prof_n, 1)
     bytes_per_launch = algo[1] * nv
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    if args.prof_class == PROF_SL_FWD and SL_FWD_TRAFFIC_192 is not None:
+        traffic = round(SL_FWD_TRAFFIC_192 * (n / 192.0) ** 3)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None, "kernel": algo[0],
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "traffic_note": "bytes per launch from an ncu capture at 192^3 scaled by voxel count",
+                "kernel": algo[0],
                 "bytes_per_launch": bytes_per_launch, "launches": prof_n, "mean_launch_ms": per_launch_ms,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"}
 
@@ -270,6 +282,33 @@ def main():
         tts = {"tts_s": time.perf_counter() - t0, "iters": stt.iters, "converged": bool(stt.converged),
                "rel_grad_inf": stt.rel_grad_inf, "grad_evals": stt.grad_evals, "obj_evals": stt.obj_evals,
                "pde_solves": stt.pde_solves, "mismatch": stt.mismatch, "obj": stt.obj, "error": err}
+
+    # ---- the same solve on the FP64 GPU path (optional) ----
+    fp64 = None
+    if args.fp64_tts:
+        P.close()
+        torch.cuda.empty_cache()
+        d64 = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+        P64 = ga.Problem(d64(w["m0"]), d64(w["m1"]), prec="fp64", **SETTINGS)
+        v64 = torch.zeros((3,) + shape, dtype=torch.float64, device="cuda")
+        barrier()
+        t0 = time.perf_counter()
+        try:
+            s64, _ = P64.solve(v64)
+            err = None
+        except ga.GaError as e:
+            err = str(e)
+            s64 = ga.Stats()
+            ga.lib().ga_get_stats(P64.ctx, s64)
+        torch.cuda.synchronize()
+        fp64 = {"tts_s": time.perf_counter() - t0, "iters": s64.iters, "converged": bool(s64.converged),
+                "rel_grad_inf": s64.rel_grad_inf, "grad_evals": s64.grad_evals, "obj_evals": s64.obj_evals,
+                "t_grad_ms_per_eval": s64.t_grad_ms / max(s64.grad_evals, 1), "error": err}
+        P64.close()
+        del P64, v64
+        torch.cuda.empty_cache()
+        P = ga.Problem(m0, m1, prec="mixed", **SETTINGS)
+        v.zero_()
 
     # ---- pure gradient throughput (ga_gradient only) ----
     g = torch.empty_like(v)
@@ -324,7 +363,7 @@ def main():
                            "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "tts": tts, "grad_only_evals_per_s": grad_only,
+                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in
                                                                        ("iters", "obj_evals", "rel_grad_inf", "obj",
                                                                         "rho_mem")}}
