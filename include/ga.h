@@ -134,9 +134,12 @@ ga_status ga_solve(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats);
 /* Forget the iteration state (k = 0, empty window, rho memory = 1); data stay. */
 ga_status ga_reset(ga_ctx* ctx);
 
-/* Solve `count` independent problems (each with its own context) one after another on their
- * streams; stats[i] receives each problem's statistics. Returns the first non-OK status other
- * than GA_ERR_NOT_CONVERGED, else GA_ERR_NOT_CONVERGED if any problem hit its cap, else GA_OK. */
+/* Solve `count` independent problems, each with its own context (the batched form of the solver):
+ * the problems are driven concurrently by host workers, each on its own context's stream, so their
+ * kernels overlap on the GPU; give every context its own stream for the overlap to happen. Contexts
+ * must be distinct. v[i] is problem i's v_inout (all in memory `mem`); stats[i] (may be NULL)
+ * receives its statistics. Returns the first non-OK status other than GA_ERR_NOT_CONVERGED in
+ * problem order, else GA_ERR_NOT_CONVERGED if any problem hit its cap, else GA_OK. */
 ga_status ga_solve_batch(int count, ga_ctx* const* ctxs, void* const* v, int mem, ga_stats* stats);
 
 ga_status ga_get_stats(const ga_ctx* ctx, ga_stats* stats);

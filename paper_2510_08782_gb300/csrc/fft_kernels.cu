@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "fft_core.cuh"
@@ -404,9 +405,24 @@ template <typename T, typename F> cudaError_t with_nc(int L, F&& f) {
   return f(std::integral_constant<int, 0>());
 }
 
+// Opt a kernel into large dynamic shared memory. The limit is a process-wide property of the kernel,
+// so it is always raised to the device's opt-in maximum (never to one launch's size): concurrent
+// host threads launching the same kernel with different sizes cannot lower it under each other.
+inline int smem_optin_max() {
+  static std::once_flag once;
+  static int bytes = 48 * 1024;
+  std::call_once(once, [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
+      bytes = v;
+  });
+  return bytes;
+}
 template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > (size_t)smem_optin_max()) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
 }
 
 }  // namespace

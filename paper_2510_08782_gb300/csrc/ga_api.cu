@@ -11,6 +11,8 @@
 // and the combination run on the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -18,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -811,13 +814,32 @@ ga_status ga_solve(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
 
 ga_status ga_solve_batch(int count, ga_ctx* const* ctxs, void* const* v, int mem, ga_stats* stats) {
   if (count < 0 || (count > 0 && (!ctxs || !v))) return GA_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i] || !v[i]) return GA_ERR_ARG;
+  // Each problem is solved by its own host worker on its own context stream, so the kernels of
+  // different problems overlap on the GPU while any one of them waits for a line-search decision.
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<ga_status> st(count, GA_OK);
+  std::atomic<int> next{0};
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nworkers = std::max(1, std::min(count, (int)std::min(32u, hw ? hw : 8u)));
+  auto worker = [&] {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1))
+      st[i] = ga_solve(ctxs[i], v[i], mem, stats ? &stats[i] : nullptr);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nworkers; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
   ga_status worst = GA_OK;
   for (int i = 0; i < count; ++i) {
-    ga_status s = ga_solve(ctxs[i], v[i], mem, stats ? &stats[i] : nullptr);
-    if (s == GA_ERR_NOT_CONVERGED) {
-      if (worst == GA_OK) worst = s;
-    } else if (s != GA_OK) {
-      return s;
+    if (st[i] == GA_ERR_NOT_CONVERGED) {
+      if (worst == GA_OK) worst = st[i];
+    } else if (st[i] != GA_OK) {
+      ga::set_global_error(("problem " + std::to_string(i) + ": " + ctxs[i]->err).c_str());
+      return st[i];
     }
   }
   return worst;

@@ -9,6 +9,7 @@
 // exactly.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "kernels.h"
@@ -278,11 +279,11 @@ cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const fl
                         cudaStream_t st) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
   const size_t sm = sizeof(float) * TILEA * NF;  // two-field steps: TILEA float2 pairs
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {
     cudaError_t e = cudaFuncSetAttribute(k_sl_tile<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.store(true);
   }
   const int nb = ((g.n[2] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[0] + BZ - 1) / BZ);
   // 16-byte copies need n2 % 4 == 0 (rows of whole chunks), no chunk across the periodic seam
@@ -299,11 +300,11 @@ cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const fl
 cudaError_t launch_departure_tile(const Grid& g, const float* v, float* xm, float* xp, float ht, int both,
                                   cudaStream_t st) {
   const size_t sm = sizeof(float) * TILEA * 3;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {
     cudaError_t e = cudaFuncSetAttribute(k_departure_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.store(true);
   }
   const int nb = ((g.n[2] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[0] + BZ - 1) / BZ);
   const bool aligned = (reinterpret_cast<uintptr_t>(v) & 15u) == 0;
