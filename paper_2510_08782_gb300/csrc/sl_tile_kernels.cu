@@ -72,20 +72,17 @@ __device__ __forceinline__ void gather_global(const float* __restrict__ f, const
   S = accp;
 }
 
+// Output of one step from P = I[f], S = I[f mu] at the departure point and m = mu at the voxel.
+template <int MODE> __device__ __forceinline__ float step_value(float P, float S, float m, float ht) {
+  if (MODE == 1) return P - 0.5f * ht * (S + m * (P - ht * S));
+  if (MODE == 2) return P + 0.5f * ht * (S + m * (P + ht * S));
+  return P;
+}
+
 template <int MODE>
 __device__ __forceinline__ void store_step(float* __restrict__ out, const float* __restrict__ mu, long long idx,
                                            float P, float S, float ht) {
-  float o;
-  if (MODE == 1) {
-    const float m = mu[idx];
-    o = P - 0.5f * ht * (S + m * (P - ht * S));
-  } else if (MODE == 2) {
-    const float m = mu[idx];
-    o = P + 0.5f * ht * (S + m * (P + ht * S));
-  } else {
-    o = P;
-  }
-  out[idx] = o;
+  out[idx] = step_value<MODE>(P, S, (MODE == 1 || MODE == 2) ? mu[idx] : 0.f, ht);
 }
 
 // ---- asynchronous global -> shared copies (LDGSTS) ----
@@ -141,23 +138,101 @@ __device__ __forceinline__ void stage_async(float* dst, const float* __restrict_
   }
 }
 
+// ---- scalar / packed-pair arithmetic with explicit rounding ----
+// The pair type float2 runs two independent lanes through the FP32x2 FMA path of sm_100+; the scalar
+// overloads perform the same operations in the same order, so a voxel's interpolant does not depend
+// on whether it was computed alone or in a pair.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <typename V> __device__ __forceinline__ V vsplat(float c);
+template <> __device__ __forceinline__ float vsplat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 vsplat<float2>(float c) { return make_float2(c, c); }
+
+// Cubic Lagrange weights on the nodes -1, 0, 1, 2 at offset t in [0, 1):
+// w_-1 = -t(t-1)(t-2)/6, w_0 = (t+1)(t-1)(t-2)/2, w_1 = -(t+1)t(t-2)/2, w_2 = (t+1)t(t-1)/6.
+template <typename V> __device__ __forceinline__ void lagrange4v(V t, V* w) {
+  const V tp1 = vadd(t, vsplat<V>(1.f)), tm1 = vadd(t, vsplat<V>(-1.f)), tm2 = vadd(t, vsplat<V>(-2.f));
+  const V a = vmul(t, tm1), b = vmul(tp1, tm2);
+  w[0] = vmul(vmul(a, tm2), vsplat<V>(-1.f / 6.f));
+  w[1] = vmul(vmul(b, tm1), vsplat<V>(0.5f));
+  w[2] = vmul(vmul(b, t), vsplat<V>(-0.5f));
+  w[3] = vmul(vmul(a, tp1), vsplat<V>(1.f / 6.f));
+}
+
+// Tensor-product sum of the 4 x 4 x 4 taps returned by ld(offset) (offset relative to the stencil's
+// first tap, in tile elements): 16 rows along x, then 4 columns along y, then z.
+template <typename V, typename Load>
+__device__ __forceinline__ V interp64(const V* wz, const V* wy, const V* wx, Load ld) {
+  V acc;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    V ay;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int o = (c * TY + b) * TXA;
+      V r = vmul(ld(o), wx[0]);
+      r = vfma(ld(o + 1), wx[1], r);
+      r = vfma(ld(o + 2), wx[2], r);
+      r = vfma(ld(o + 3), wx[3], r);
+      ay = b == 0 ? vmul(r, wy[0]) : vfma(r, wy[b], ay);
+    }
+    acc = c == 0 ? vmul(ay, wz[0]) : vfma(ay, wz[c], acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ bool in_halo(float fz, float fy, float fx) {
+  return fz >= -H && fz <= H - 1 && fy >= -H && fy <= H - 1 && fx >= -H && fx <= H - 1;
+}
+
+// One voxel (brick-local z index v, global index idx): shared-memory taps when the stencil lies in the
+// halo, global taps otherwise.
+template <int MODE>
+__device__ __forceinline__ void sl_single(const float* __restrict__ f, const float* __restrict__ mu,
+                                          float* __restrict__ out, const float* sf, const float* sg, int col,
+                                          long long idx, int gz, int v, int gy, int gx, float vz, float vy, float vx,
+                                          int n0, int n1, int n2, float ht) {
+  constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
+  const float fz = floorf(vz), fy = floorf(vy), fx = floorf(vx);
+  float P = 0.f, S = 0.f;
+  if (in_halo(fz, fy, fx)) {
+    float wz[4], wy[4], wx[4];
+    lagrange4v(vz - fz, wz);
+    lagrange4v(vy - fy, wy);
+    lagrange4v(vx - fx, wx);
+    const int base = col + ((v + H + (int)fz) * TY + (int)fy) * TXA + (int)fx;
+    P = interp64<float>(wz, wy, wx, [&](int o) { return sf[base + o]; });
+    if (NF == 2) S = interp64<float>(wz, wy, wx, [&](int o) { return sg[base + o]; });
+  } else {
+    gather_global<NF>(f, mu, gz, gy, gx, vz, vy, vx, n0, n1, n2, P, S);
+  }
+  store_step<MODE>(out, mu, idx, P, S, ht);
+}
+
 // MODE 0: advection state step          out = I[f](X-)
 // MODE 1: continuity state step         out = P - ht/2 (S + mu (P - ht S)),  P = I[f], S = I[f mu]
 // MODE 2: advection adjoint step        out = L + ht/2 (S + mu (L + ht S)),  L = I[f], S = I[f mu]
 // MODE 3: continuity adjoint step       out = I[f](X+)
 // One CTA per brick. The tile (and, for the two-field steps, mu) is copied asynchronously into
-// shared memory; several CTAs per SM overlap one brick's copies with another's interpolation. Each
-// thread interpolates its column of 8 voxels one voxel at a time: the 64 taps are read from shared
+// shared memory; several CTAs per SM overlap one brick's copies with another's interpolation. For
+// the two-field steps the staged mu tile is then overwritten with f * mu, so the product is formed
+// once per tile element. Each thread walks its column of 8 voxels two at a time: the pair's weights
+// and its 64-tap sums (per field) run as packed FP32x2 operations, with the taps read from shared
 // memory at compile-time offsets from one base index per voxel.
 template <int MODE>
-__global__ void __launch_bounds__(256)
-k_sl_tile(const float* __restrict__ f, const float* __restrict__ mu, const float* __restrict__ disp,
-          float* __restrict__ out, int n0, int n1, int n2, float ht, int vec) {
-  constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;  // staged fields: f (and mu)
+__device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const float* __restrict__ mu,
+                                             const float* __restrict__ disp, float* __restrict__ out, int n0, int n1,
+                                             int n2, float ht, int vec) {
+  constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;  // staged fields: f (and f * mu)
   extern __shared__ __align__(16) float smem[];
   const float* sf = smem;
-  const float* sm = smem + TILEA;
+  const float* sg = smem + TILEA;
   const long long nv = (long long)n0 * n1 * n2;
+  const long long plane = (long long)n1 * n2;
   const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
   const BrickIdx bi = brick_of(blockIdx.x, nbx, nby);
   stage_async(smem, f, bi, n0, n1, n2, vec != 0);
@@ -165,42 +240,75 @@ k_sl_tile(const float* __restrict__ f, const float* __restrict__ mu, const float
   cp_async_commit();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gx = bi.bx * BX + lane, gy = bi.by * BY + warp;
+  const bool active = gx < n2 && gy < n1;
+  const int nz = min(BZ, n0 - bi.bz * BZ);
+  const long long idx0 = ((long long)(bi.bz * BZ) * n1 + gy) * n2 + gx;
+  // Displacements (and mu at the voxel) of one pair ahead are kept in registers: the first pair's are
+  // requested while the tile is still being copied, each later pair's while the previous one is
+  // interpolated.
+  float za = 0.f, zb = 0.f, ya = 0.f, yb = 0.f, xa = 0.f, xb = 0.f, ma = 0.f, mb = 0.f;
+  auto fetch = [&](int v) {
+    const long long ia = idx0 + v * plane, ib = ia + plane;
+    za = disp[ia], zb = disp[ib];
+    ya = disp[nv + ia], yb = disp[nv + ib];
+    xa = disp[2 * nv + ia], xb = disp[2 * nv + ib];
+    if (NF == 2) ma = mu[ia], mb = mu[ib];
+  };
+  if (active && nz >= 2) fetch(0);
   asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
-  if (gx >= n2 || gy >= n1) return;
-  const int nz = min(BZ, n0 - bi.bz * BZ);
-#pragma unroll 2
-  for (int v = 0; v < nz; ++v) {
-    const long long idx = ((long long)(bi.bz * BZ + v) * n1 + gy) * n2 + gx;
-    const float vz = disp[idx], vy = disp[nv + idx], vx = disp[2 * nv + idx];
-    const float fz = floorf(vz), fy = floorf(vy), fx = floorf(vx);
-    float P = 0.f, S = 0.f;
-    if (fz >= -H && fz <= H - 1 && fy >= -H && fy <= H - 1 && fx >= -H && fx <= H - 1) {
-      float wz[4], wy[4], wx[4];
-      lagrange4(vz - fz, wz);
-      lagrange4(vy - fy, wy);
-      lagrange4(vx - fx, wx);
-      const int base = ((v + H + (int)fz) * TY + warp + H + (int)fy) * TXA + lane + XOFF - 1 + (int)fx;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float ay = 0.f, ayp = 0.f;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int o = base + (c * TY + b) * TXA;
-          const float f0 = sf[o], f1 = sf[o + 1], f2 = sf[o + 2], f3 = sf[o + 3];
-          ay += wy[b] * (wx[0] * f0 + wx[1] * f1 + wx[2] * f2 + wx[3] * f3);
-          if (NF == 2)
-            ayp += wy[b] * (wx[0] * f0 * sm[o] + wx[1] * f1 * sm[o + 1] + wx[2] * f2 * sm[o + 2] +
-                            wx[3] * f3 * sm[o + 3]);
-        }
-        P += wz[c] * ay;
-        if (NF == 2) S += wz[c] * ayp;
-      }
-    } else {
-      gather_global<NF>(f, mu, bi.bz * BZ + v, gy, gx, vz, vy, vx, n0, n1, n2, P, S);
-    }
-    store_step<MODE>(out, mu, idx, P, S, ht);
+  if (NF == 2) {  // each element is read and written by one thread only
+    for (int e = threadIdx.x; e < TILEA; e += blockDim.x) smem[TILEA + e] *= smem[e];
+    __syncthreads();
   }
+  if (!active) return;
+  const int col = (warp + H) * TXA + lane + XOFF - 1;  // tile index of (z = 0, y, x) minus the x tap offset
+
+  int v = 0;
+#pragma unroll 1
+  for (; v + 1 < nz; v += 2) {
+    const long long ia = idx0 + v * plane, ib = ia + plane;
+    const float cza = za, czb = zb, cya = ya, cyb = yb, cxa = xa, cxb = xb, cma = ma, cmb = mb;
+    if (v + 3 < nz) fetch(v + 2);
+    const float fza = floorf(cza), fya = floorf(cya), fxa = floorf(cxa);
+    const float fzb = floorf(czb), fyb = floorf(cyb), fxb = floorf(cxb);
+    if (in_halo(fza, fya, fxa) && in_halo(fzb, fyb, fxb)) {
+      float2 wz[4], wy[4], wx[4];
+      lagrange4v(make_float2(cza - fza, czb - fzb), wz);
+      lagrange4v(make_float2(cya - fya, cyb - fyb), wy);
+      lagrange4v(make_float2(cxa - fxa, cxb - fxb), wx);
+      const int ba = col + ((v + H + (int)fza) * TY + (int)fya) * TXA + (int)fxa;
+      const int bb = col + ((v + 1 + H + (int)fzb) * TY + (int)fyb) * TXA + (int)fxb;
+      const float2 P = interp64<float2>(wz, wy, wx, [&](int o) { return make_float2(sf[ba + o], sf[bb + o]); });
+      float2 S = make_float2(0.f, 0.f);
+      if (NF == 2) S = interp64<float2>(wz, wy, wx, [&](int o) { return make_float2(sg[ba + o], sg[bb + o]); });
+      out[ia] = step_value<MODE>(P.x, S.x, cma, ht);
+      out[ib] = step_value<MODE>(P.y, S.y, cmb, ht);
+    } else {
+      sl_single<MODE>(f, mu, out, sf, sg, col, ia, bi.bz * BZ + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
+      sl_single<MODE>(f, mu, out, sf, sg, col, ib, bi.bz * BZ + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
+    }
+  }
+  if (v < nz) {
+    const long long ia = idx0 + v * plane;
+    sl_single<MODE>(f, mu, out, sf, sg, col, ia, bi.bz * BZ + v, v, gy, gx, disp[ia], disp[nv + ia], disp[2 * nv + ia],
+                    n0, n1, n2, ht);
+  }
+}
+
+// Two-field steps (MODE 1, 2) fit 3 CTAs per SM by shared memory; one-field steps (MODE 0, 3) fit 4
+// when held to 64 registers.
+template <int MODE>
+__global__ void __launch_bounds__(256, 3) k_sl_tile2(const float* __restrict__ f, const float* __restrict__ mu,
+                                                  const float* __restrict__ disp, float* __restrict__ out, int n0,
+                                                  int n1, int n2, float ht, int vec) {
+  sl_tile_body<MODE>(f, mu, disp, out, n0, n1, n2, ht, vec);
+}
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_sl_tile1(const float* __restrict__ f, const float* __restrict__ mu,
+                                                     const float* __restrict__ disp, float* __restrict__ out, int n0,
+                                                     int n1, int n2, float ht, int vec) {
+  sl_tile_body<MODE>(f, mu, disp, out, n0, n1, n2, ht, vec);
 }
 
 // RK2 departure points (displacements in cells) for 3D FP32 grids: X* = x -/+ h_t v(x), then
@@ -278,10 +386,13 @@ template <int MODE>
 cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
                         cudaStream_t st) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
-  const size_t sm = sizeof(float) * TILEA * NF;  // two-field steps: TILEA float2 pairs
+  const size_t sm = sizeof(float) * TILEA * NF;  // two-field steps: f and f * mu tiles
+  void (*kern)(const float*, const float*, const float*, float*, int, int, int, float, int);
+  if constexpr (NF == 2) kern = k_sl_tile2<MODE>;
+  else kern = k_sl_tile1<MODE>;
   static std::atomic<bool> attr{false};
   if (!attr.load()) {
-    cudaError_t e = cudaFuncSetAttribute(k_sl_tile<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr.store(true);
   }
@@ -291,7 +402,7 @@ cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const fl
   const bool aligned = ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(mu ? mu : f)) & 15u) == 0;
   const int vec = (g.n[2] % 4 == 0 && g.n[2] >= TXA && g.n[1] >= TY && g.n[0] >= TZ && aligned) ? 1 : 0;
   note_launches(1);
-  k_sl_tile<MODE><<<nb, 256, sm, st>>>(f, mu, disp, out, g.n[0], g.n[1], g.n[2], ht, vec);
+  kern<<<nb, 256, sm, st>>>(f, mu, disp, out, g.n[0], g.n[1], g.n[2], ht, vec);
   return cudaGetLastError();
 }
 
