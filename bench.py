@@ -231,6 +231,8 @@ def main():
     ap.add_argument("--grid", type=int, default=N, help="grid size (default 256; smaller only for smoke runs)")
     ap.add_argument("--workload", default="cont3d256", choices=["cont3d256", "batch"],
                     help="cont3d256 (default) or batch: 32 independent advection problems of uneven size")
+    ap.add_argument("--compare-methods", action="store_true",
+                    help="also time the same solve with GA-AA and RPGD (mixed precision, same settings)")
     ap.add_argument("--fp64-tts", action="store_true",
                     help="also time the same GA-NGMRES solve with the FP64 GPU path (slow: FP64 is ALU-bound on GB300)")
     args = ap.parse_args()
@@ -327,6 +329,20 @@ def main():
                 "kernel": algo[0],
                 "bytes_per_launch": bytes_per_launch, "launches": prof_n, "mean_launch_ms": per_launch_ms,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"}
+    # The semi-Lagrangian steps are bound by shared-memory bandwidth, not HBM: each interpolated field
+    # reads 64 taps x 4 B per voxel from the staged tile. Peak: 128 B per clock per SM at the median SM
+    # clock sampled during the timed region.
+    taps_fields = {PROF_SL_FWD: 2, PROF_SL_ADJ: 1}.get(args.prof_class)
+    if taps_fields:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+        smem_peak = sms * 128 * mhz * 1e6 / 1e9
+        smem_bytes = 64 * 4 * taps_fields * nv
+        smem_achieved = smem_bytes / (per_launch_ms / 1e3) / 1e9
+        roofline["secondary"] = {"bound": "smem", "achieved": round(smem_achieved, 1), "peak": round(smem_peak, 1),
+                                 "unit": "GB/s", "frac": round(smem_achieved / smem_peak, 4),
+                                 "bytes_per_launch": smem_bytes,
+                                 "peak_kind": f"nominal: {sms} SMs x 128 B/clock x {mhz:.0f} MHz (sampled)"}
 
     # ---- time to rel-grad 1e-2 from v = 0 (GA-NGMRES) ----
     tts = None
@@ -372,6 +388,34 @@ def main():
         del P64, v64
         torch.cuda.empty_cache()
         P = ga.Problem(m0, m1, prec="mixed", **SETTINGS)
+        v.zero_()
+
+    # ---- the same solve with the other methods of the paper's comparison (optional) ----
+    methods = None
+    if args.compare_methods:
+        methods = {}
+        for meth in ("ga-aa", "rpgd"):
+            P.close()
+            torch.cuda.empty_cache()
+            Pm = ga.Problem(m0, m1, prec="mixed", method=meth, **SETTINGS)
+            vm = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
+            barrier()
+            t0 = time.perf_counter()
+            try:
+                sm, _ = Pm.solve(vm)
+                err = None
+            except ga.GaError as e:
+                err = str(e)
+                sm = ga.Stats()
+                ga.lib().ga_get_stats(Pm.ctx, sm)
+            torch.cuda.synchronize()
+            methods[meth] = {"tts_s": time.perf_counter() - t0, "iters": sm.iters, "converged": bool(sm.converged),
+                             "rel_grad_inf": sm.rel_grad_inf, "grad_evals": sm.grad_evals,
+                             "obj_evals": sm.obj_evals, "error": err}
+            Pm.close()
+            del Pm, vm
+            torch.cuda.empty_cache()
+            P = ga.Problem(m0, m1, prec="mixed", **SETTINGS)
         v.zero_()
 
     # ---- pure gradient throughput (ga_gradient only) ----
@@ -427,7 +471,7 @@ def main():
                            "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "grad_only_evals_per_s": grad_only,
+                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "methods_tts": methods, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in
                                                                        ("iters", "obj_evals", "rel_grad_inf", "obj",
                                                                         "rho_mem")}}

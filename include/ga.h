@@ -52,7 +52,9 @@ typedef enum {
 
 typedef enum { GA_PREC_FP64 = 0, GA_PREC_MIXED = 1 } ga_precision;
 typedef enum { GA_MEM_HOST = 0, GA_MEM_DEVICE = 1 } ga_mem;
-typedef enum { GA_METHOD_GA_NGMRES = 0, GA_METHOD_RPGD = 1 } ga_method;
+/* GA_METHOD_GA_AA: Anderson acceleration AA(w) (Alg. 2) on the map q with the mixing schedule of
+ * Alg. 3 (GA-AA; Sec. 2.3.2 and Sec. 3.3 compare it with GA-NGMRES). */
+typedef enum { GA_METHOD_GA_NGMRES = 0, GA_METHOD_RPGD = 1, GA_METHOD_GA_AA = 2 } ga_method;
 
 /* Problem description (Sec. 1.1 problem statement, Sec. 2.2 discretisation). */
 typedef struct {
@@ -121,7 +123,7 @@ ga_status ga_gradient(ga_ctx* ctx, const void* v, void* g, int mem, double* obj)
  * (Sec. 2.2, Eq. (9)); incompressible model: s = -(alpha L)^{-1} P g. */
 ga_status ga_precond(ga_ctx* ctx, const void* g, void* s, int mem);
 
-/* One iteration of Alg. 3 (GA-NGMRES(w; sigma, tau)) or of RPGD (Eq. (9)), including the
+/* One iteration of Alg. 3 (GA-NGMRES(w; sigma, tau)), of RPGD (Eq. (9)) or of GA-AA, including the
  * Armijo line search with step memory that defines q (Eq. (10)). The first call after setup or
  * ga_reset takes v^(0) from v_inout; every call writes v^(k+1) to v_inout. stats may be NULL. */
 ga_status ga_step(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats);

@@ -16,7 +16,7 @@ import numpy as np
 GA_MODEL_ADVECTION, GA_MODEL_CONTINUITY, GA_MODEL_INCOMPRESSIBLE = 0, 1, 2
 GA_PREC_FP64, GA_PREC_MIXED = 0, 1
 GA_MEM_HOST, GA_MEM_DEVICE = 0, 1
-GA_METHOD_GA_NGMRES, GA_METHOD_RPGD = 0, 1
+GA_METHOD_GA_NGMRES, GA_METHOD_RPGD, GA_METHOD_GA_AA = 0, 1, 2
 STATUS = {0: "GA_OK", 1: "GA_ERR_ARG", 2: "GA_ERR_CUDA", 3: "GA_ERR_NOMEM", 4: "GA_ERR_NAN",
           5: "GA_ERR_LINESEARCH", 6: "GA_ERR_NOT_CONVERGED", 7: "GA_ERR_TIMEOUT"}
 MODELS = {"advection": GA_MODEL_ADVECTION, "continuity": GA_MODEL_CONTINUITY,
@@ -369,7 +369,10 @@ class Problem:
         o.window, o.sigma, o.tau, o.max_iter = int(window), int(sigma), int(tau), int(max_iter)
         o.rel_tol, o.armijo_c, o.max_backtracks = float(rel_tol), float(armijo_c), int(max_backtracks)
         o.variant = int(variant)
-        o.method = GA_METHOD_RPGD if method == "rpgd" else GA_METHOD_GA_NGMRES
+        methods = {"ga-ngmres": GA_METHOD_GA_NGMRES, "rpgd": GA_METHOD_RPGD, "ga-aa": GA_METHOD_GA_AA}
+        if method not in methods:
+            raise ValueError(f"method must be one of {sorted(methods)}")
+        o.method = methods[method]
         self.desc, self.opts = d, o
         self.ctx = ga_setup(d, o, m0, m1, stream)
 

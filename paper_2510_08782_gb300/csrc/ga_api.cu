@@ -460,6 +460,14 @@ template <typename T> struct Engine : EngineBase {
       gfree.push_back(win.back().second);
       win.pop_back();
     }
+    while (!awin.empty()) {
+      vfree.push_back(awin.back().first);
+      gfree.push_back(awin.back().second);
+      awin.pop_back();
+    }
+    if (cur_v) vfree.push_back(cur_v);
+    if (cur_g) gfree.push_back(cur_g);
+    cur_v = cur_g = nullptr;
     started = false;
     s_valid = false;
     k = 0;
@@ -492,6 +500,37 @@ template <typename T> struct Engine : EngineBase {
     win.push_front({v, gv});
   }
 
+  // GA-AA state: the current iterate and its gradient, and the previous (q_j, r_j = v_j - q_j),
+  // newest first, at most w entries; dM then holds the Gram matrix of the window residuals.
+  std::deque<std::pair<T*, T*>> awin;
+  T* cur_v = nullptr;
+  T* cur_g = nullptr;
+
+  bool aa() const { return ctx->opts.method == GA_METHOD_GA_AA; }
+  T* current() const { return aa() ? cur_v : win.front().first; }
+
+  // Append (q, r) as the newest GA-AA window entry, dropping the oldest beyond w entries.
+  void push_aa(T* q, T* r) {
+    if (W1 == 1) {  // w = 0: nothing is kept
+      vfree.push_back(q);
+      gfree.push_back(r);
+      return;
+    }
+    int keep = (int)awin.size();
+    if (keep == W1 - 1) {
+      vfree.push_back(awin.back().first);
+      gfree.push_back(awin.back().second);
+      awin.pop_back();
+      keep = W1 - 2;
+    }
+    std::vector<const T*> bl;
+    bl.push_back(r);
+    for (int i = 0; i < keep; ++i) bl.push_back(awin[i].second);
+    ck(launch_dots<T>(r, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "window dots");
+    ck(launch_gram_push(dM, W1, keep, dres + 16, st), "gram push");
+    awin.push_front({q, r});
+  }
+
   bool is_fp_step(int kk) const {
     const ga_solver_opts& o = ctx->opts;
     if (o.method == GA_METHOD_RPGD) return true;
@@ -507,7 +546,12 @@ template <typename T> struct Engine : EngineBase {
     J = gradient(v, gv, S, &mis);
     s_valid = true;
     g0inf = last_ginf;
-    push_window(v, gv);
+    if (aa()) {
+      cur_v = v;
+      cur_g = gv;
+    } else {
+      push_window(v, gv);
+    }
     started = true;
     ga_stats& stt = ctx->stats;
     stt.obj = J;
@@ -517,14 +561,13 @@ template <typename T> struct Engine : EngineBase {
     stt.rho_mem = rho_mem;
   }
 
-  // One iteration k of Alg. 3. The current iterate is the newest window entry.
-  void step() {
+  // q(v) = v + rho s by the Armijo line search with step memory (Eqs. (6)-(7), Sec. 2.3), s = S the
+  // preconditioned direction at v. Returns the accepted trial in a buffer of the v pool; its state
+  // trajectory stays cached for a gradient evaluation at exactly that buffer.
+  T* qmap(const T* v, const T* gv) {
     const ga_solver_opts& o = ctx->opts;
     ga_stats& stt = ctx->stats;
-    T* v = win.front().first;
-    T* gv = win.front().second;
     if (!s_valid) precond(gv, S);
-    // Armijo line search with step memory (Eqs. (6)-(7), Sec. 2.3)
     const double gs = dot_l2(gv, S);
     T* q = take(vfree);
     double rho = rho_mem, Jq = 0.0;
@@ -547,6 +590,77 @@ template <typename T> struct Engine : EngineBase {
     }
     stt.last_rho = rho;
     stt.rho_mem = rho_mem;
+    return q;
+  }
+
+  void finish_step(bool fp, double Jn, double misn) {
+    const ga_solver_opts& o = ctx->opts;
+    ga_stats& stt = ctx->stats;
+    s_valid = true;
+    J = Jn;
+    ++k;
+    stt.iters = k;
+    stt.last_branch = fp ? 1 : 0;
+    stt.obj = Jn;
+    stt.mismatch = misn;
+    stt.rel_grad_inf = g0inf > 0 ? last_ginf / g0inf : 0.0;
+    stt.converged = stt.rel_grad_inf <= o.rel_tol ? 1 : 0;
+  }
+
+  // One iteration k of GA-AA(w; sigma, tau): Anderson acceleration AA(w) (Alg. 2) on the fixed-point
+  // map q with the mixing schedule of Alg. 3. With r_j = v_j - q(v_j), the coefficients xi minimise
+  // ||r_k + sum_{i=1..w^(k)} xi_i (r_k - r_{k-i})|| and v_{k+1} = q_k + sum_i xi_i (q_k - q_{k-i});
+  // a fixed-point step (or an empty window) takes v_{k+1} = q_k. Both kinds of step enter the window.
+  void step_aa() {
+    T* v = cur_v;
+    T* gv = cur_g;
+    T* q = qmap(v, gv);
+    T* r = take(gfree);
+    ck(launch_axpy<T>(r, v, q, -1.0, vl, st), "residual");
+    const bool fp = is_fp_step(k) || awin.empty();
+    T *vn, *gn = take(gfree);
+    double Jn, misn;
+    if (fp) {
+      Jn = gradient(q, gn, S, &misn);  // reuses the accepted trial's state trajectory
+      vn = q;
+      if (W1 > 1) {
+        T* qw = take(vfree);
+        ck(cudaMemcpyAsync(qw, q, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy q");
+        push_aa(qw, r);
+      } else {
+        gfree.push_back(r);
+      }
+    } else {
+      const int m = (int)awin.size();  // w^(k) previous entries
+      std::vector<const T*> bl;
+      bl.push_back(r);
+      for (int i = 0; i < m; ++i) bl.push_back(awin[i].second);
+      ck(launch_dots<T>(r, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "lsq dots");
+      ck(launch_lsq(m, dres + 16, dM, W1, dbeta, dres + 56, st), "lsq");
+      vn = take(vfree);
+      std::vector<const T*> qlst;
+      for (int i = 0; i < m; ++i) qlst.push_back(awin[i].first);
+      ck(launch_combine<T>(vn, q, qlst.data(), dbeta, m, vl, st), "combine");
+      push_aa(q, r);  // stream order keeps a dropped entry intact until the combination has read it
+      Jn = gradient(vn, gn, S, &misn);
+    }
+    vfree.push_back(cur_v);
+    gfree.push_back(cur_g);
+    cur_v = vn;
+    cur_g = gn;
+    finish_step(fp, Jn, misn);
+  }
+
+  // One iteration k of Alg. 3 (or of RPGD, or of GA-AA). For GA-NGMRES and RPGD the current iterate
+  // is the newest window entry.
+  void step() {
+    if (aa()) {
+      step_aa();
+      return;
+    }
+    T* v = win.front().first;
+    T* gv = win.front().second;
+    T* q = qmap(v, gv);
     const bool fp = is_fp_step(k);
     T* gq = take(gfree);
     T *vn, *gn;
@@ -573,16 +687,8 @@ template <typename T> struct Engine : EngineBase {
       gn = take(gfree);
       Jn = gradient(vn, gn, S, &misn);
     }
-    s_valid = true;
     push_window(vn, gn);
-    J = Jn;
-    ++k;
-    stt.iters = k;
-    stt.last_branch = fp ? 1 : 0;
-    stt.obj = Jn;
-    stt.mismatch = misn;
-    stt.rel_grad_inf = g0inf > 0 ? last_ginf / g0inf : 0.0;
-    stt.converged = stt.rel_grad_inf <= o.rel_tol ? 1 : 0;
+    finish_step(fp, Jn, misn);
   }
 };
 
@@ -686,7 +792,7 @@ ga_status ga_setup(const ga_problem_desc* desc, const ga_solver_opts* opts, cons
   ok = ok && o.window >= 0 && o.window < kMaxWin && o.window + 2 <= kMaxDots && o.sigma >= 1 && o.tau >= 0 &&
        o.max_iter >= 1 && o.rel_tol >= 0.0 && o.armijo_c > 0.0 && o.max_backtracks >= 0 &&
        o.max_backtracks <= 200 && (o.variant == 1 || o.variant == 2) &&
-       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD);
+       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD || o.method == GA_METHOD_GA_AA);
   if (!ok) {
     g_setup_err = "invalid problem descriptor or solver options";
     return GA_ERR_ARG;
@@ -783,7 +889,7 @@ ga_status ga_step(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
       e.start(vin);
     }
     e.step();
-    stage_out(e, v_inout, e.win.front().first, e.vl, mem);
+    stage_out(e, v_inout, e.current(), e.vl, mem);
   });
   ctx->stats.t_total_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = ctx->stats;
@@ -804,7 +910,7 @@ ga_status ga_solve(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
     } else {
       ctx->stats.converged = 1;
     }
-    stage_out(e, v_inout, e.win.front().first, e.vl, mem);
+    stage_out(e, v_inout, e.current(), e.vl, mem);
   });
   ctx->stats.t_total_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = ctx->stats;

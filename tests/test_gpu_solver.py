@@ -60,6 +60,41 @@ def test_iterates_match_oracle_fp64(variant):
     assert abs(st.rho_mem - q.rho_mem) == 0.0
 
 
+@pytest.mark.parametrize("variant,sigma,tau", [(1, 2, 1), (2, 2, 1), (1, 1, 1)])
+def test_ga_aa_iterates_match_oracle_fp64(variant, sigma, tau):
+    """GA-AA(3; sigma, tau) (Anderson acceleration on q with the mixing of Alg. 3): the residual
+    window, its least squares and the combination of the q's reproduce the oracle's iterates."""
+    w = workload("adv2d64", n=(32, 32))
+    P, O, so = _pair(w, "fp64", window=3, sigma=sigma, tau=tau, max_iter=8, variant=variant, method="ga-aa")
+    v = to_dev(np.zeros((2, 32, 32)), "fp64")
+    hist = []
+    q = osol.ArmijoQ(O)
+    osol.ga_aa(O.gradient, q, np.zeros((2, 32, 32)), window=3, sigma=sigma, tau=tau, n_iter=7, rel_tol=0.0,
+               variant=variant, history=hist)
+    assert any(h["branch"] == "aa" for h in hist)
+    for k, h in enumerate(hist):
+        st = P.step(v)
+        assert st.iters == k + 1
+        assert st.last_branch == (1 if h["branch"] == "fp" else 0)
+        err = rel_l2(host(v), h["v"])
+        assert err < 1e-8, (k, err)
+        assert abs(st.obj - h["obj"]) <= 1e-9 * abs(h["obj"])
+    assert abs(st.rho_mem - q.rho_mem) == 0.0
+
+
+def test_ga_aa_window_zero_is_rpgd():
+    """With w = 0 every GA-AA step is a fixed-point step, so the iterates are those of RPGD."""
+    w = workload("adv2d64", n=(32, 32))
+    P1, _, _ = _pair(w, "fp64", window=0, max_iter=5, method="ga-aa")
+    P2, _, _ = _pair(w, "fp64", window=0, max_iter=5, method="rpgd")
+    v1 = to_dev(np.zeros((2, 32, 32)), "fp64")
+    v2 = to_dev(np.zeros((2, 32, 32)), "fp64")
+    for _ in range(4):
+        s1, s2 = P1.step(v1), P2.step(v2)
+        assert s1.last_branch == 1 and s2.last_branch == 1
+        assert np.array_equal(host(v1), host(v2))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_full_solve_matches_oracle_adv2d64(prec):
     """2D 64x64 advection workload (8 blobs, H1, alpha 1e-2, w 5, (4,2)), solved to rel-grad 1e-2."""
