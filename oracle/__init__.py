@@ -13,6 +13,8 @@ Modules
   problem    objective (Eq. (1a)), reduced gradient (Eq. (3)), preconditioner (Eq. (9)) per model
   solver     Armijo line search with step memory (Eqs. (6)-(7)), q map (Eq. (10)), NGMRES(w) (Alg. 1),
              AA(w) (Alg. 2), GA-NGMRES(w; sigma, tau) (Alg. 3), dense GMRES for the linear-case pins
+  diagnostics  deformation map y = x + h u and det grad y (continuity solve from 1), with a spectral
+             det(I + grad(h u)) cross-check route
 
 Readings of passages the paper leaves silent, garbled or ambiguous are stated in each
 function's docstring. Parity status: every function is pinned by a CPU test against a
