@@ -363,6 +363,23 @@ def main():
                "rel_grad_inf": stt.rel_grad_inf, "grad_evals": stt.grad_evals, "obj_evals": stt.obj_evals,
                "pde_solves": stt.pde_solves, "mismatch": stt.mismatch, "obj": stt.obj, "error": err}
 
+    # ---- deformation diagnostics of the solution: det grad y statistics, as reported with the results ----
+    deformation = None
+    if tts is not None:
+        u_def = torch.empty_like(v)
+        j_def = torch.empty(shape, dtype=v.dtype, device="cuda")
+        P.deformation(v, u_def, j_def)  # first use loads the kernels of this path
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.deformation(v, u_def, j_def)
+        torch.cuda.synchronize()
+        def_ms = (time.perf_counter() - t0) * 1e3
+        jd = j_def.double()
+        deformation = {"det_min": float(jd.min()), "det_mean": float(jd.mean()), "det_max": float(jd.max()),
+                       "det_std": float(jd.std()), "max_displacement_cells": float(u_def.abs().max()),
+                       "ms": def_ms}
+        del u_def, j_def, jd
+
     # ---- the same solve on the FP64 GPU path (optional) ----
     fp64 = None
     if args.fp64_tts:
@@ -471,7 +488,7 @@ def main():
                            "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "methods_tts": methods, "grad_only_evals_per_s": grad_only,
+                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "methods_tts": methods, "deformation": deformation, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in
                                                                        ("iters", "obj_evals", "rel_grad_inf", "obj",
                                                                         "rho_mem")}}

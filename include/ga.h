@@ -119,6 +119,15 @@ ga_status ga_objective(ga_ctx* ctx, const void* v, int mem, double* obj);
  * returns obj(v) when obj != NULL. g is a vector field (dim components). */
 ga_status ga_gradient(ga_ctx* ctx, const void* v, void* g, int mem, double* obj);
 
+/* Deformation diagnostics of a velocity v (the map y and det grad y shown with the results of
+ * Sec. 3; for incompressible flows det grad y = 1). y maps a point at t = 1 to the origin of its
+ * characteristic, so that the advected image is m(., 1) = m0(y). Outputs: u, a vector field (dim
+ * components) in grid units with y_c(x) = x_c + h_c u_c(x), from the composition of the state
+ * step's departure points, u_0 = 0, u_{j+1} = I[u_j](X-) + (X- - x); detj, a scalar field, from
+ * the continuity state solve started from 1 (the Jacobian of the inverse flow map is the density
+ * of the transported uniform measure). Uses the context's n_t and grid; 2 + dim state solves. */
+ga_status ga_deformation(ga_ctx* ctx, const void* v, void* u, void* detj, int mem);
+
 /* Preconditioned direction s = -(alpha L)^{-1} g with zero symbol entries of L set to one
  * (Sec. 2.2, Eq. (9)); incompressible model: s = -(alpha L)^{-1} P g. */
 ga_status ga_precond(ga_ctx* ctx, const void* g, void* s, int mem);

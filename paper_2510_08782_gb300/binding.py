@@ -64,6 +64,7 @@ _SIGS = {
                   ctypes.POINTER(_vp)], _c_int),
     "ga_objective": ([_vp, _vp, _c_int, ctypes.POINTER(_c_double)], _c_int),
     "ga_gradient": ([_vp, _vp, _vp, _c_int, ctypes.POINTER(_c_double)], _c_int),
+    "ga_deformation": ([_vp, _vp, _vp, _vp, _c_int], _c_int),
     "ga_precond": ([_vp, _vp, _vp, _c_int], _c_int),
     "ga_step": ([_vp, _vp, _c_int, ctypes.POINTER(Stats)], _c_int),
     "ga_solve": ([_vp, _vp, _c_int, ctypes.POINTER(Stats)], _c_int),
@@ -194,6 +195,11 @@ def ga_gradient(ctx, dtype, v, g):
     out = _c_double()
     _check(lib().ga_gradient(ctx, pv, pg, mem, ctypes.byref(out)), ctx)
     return out.value
+
+
+def ga_deformation(ctx, dtype, v, u, detj):
+    (pv, pu, pj), mem = _ptrs(dtype, v, u, detj)
+    _check(lib().ga_deformation(ctx, pv, pu, pj, mem), ctx)
 
 
 def ga_precond(ctx, dtype, g, s):
@@ -399,6 +405,10 @@ class Problem:
 
     def precond(self, g, s):
         ga_precond(self.ctx, self.dtype, g, s)
+
+    def deformation(self, v, u, detj):
+        """Displacement u (grid units) of the map y = x + h u and det grad y for the velocity v."""
+        ga_deformation(self.ctx, self.dtype, v, u, detj)
 
     def step(self, v):
         return ga_step(self.ctx, self.dtype, v)

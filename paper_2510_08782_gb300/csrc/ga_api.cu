@@ -453,6 +453,32 @@ template <typename T> struct Engine : EngineBase {
     return hd * hres[8];
   }
 
+  // ---- deformation diagnostics ------------------------------------------------------------------
+  // Displacement u (grid units, dim fields) of the map y = x + h u with m(., 1) = m0(y) and
+  // det grad y, for a stationary velocity v. y composes the state step's departure points:
+  // u_0 = 0, u_{j+1} = I[u_j](X-) + (X- - x). det grad y, the Jacobian of the inverse flow map, is
+  // the density of the transported uniform measure: the continuity state solve from 1.
+  void deformation(const T* v, T* u, T* detj) {
+    compute_mu(v);
+    ck(launch_departure<T>(g, v, xm, xp, (T)ht, st, 0), "departure");
+    ck(cudaMemsetAsync(u, 0, sizeof(T) * vl, st), "memset");
+    for (int c = 0; c < dim; ++c) {
+      T* uc = u + c * nv;
+      for (int j = 0; j < nt; ++j) {
+        ck(launch_sl_forward<T>(g, 0, uc, xm, mu, tmp[0], (T)ht, st), "sl displacement");
+        ck(launch_axpy<T>(uc, tmp[0], xm + c * nv, 1.0, nv, st), "displacement step");
+      }
+    }
+    ck(launch_fill<T>(detj, 1.0, nv, st), "fill");
+    T* a = detj;
+    T* b = tmp[0];
+    for (int j = 0; j < nt; ++j) {
+      ck(launch_sl_forward<T>(g, 1, a, xm, mu, b, (T)ht, st), "sl det");
+      std::swap(a, b);
+    }
+    if (a != detj) ck(cudaMemcpyAsync(detj, a, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st), "copy det");
+  }
+
   // ---- solver (Alg. 3) -----------------------------------------------------------------------------
   void reset() {
     while (!win.empty()) {
@@ -855,6 +881,19 @@ ga_status ga_gradient(ga_ctx* ctx, const void* v, void* g, int mem, double* obj)
     const double J = e.gradient(vin, gout, nullptr);
     if (obj) *obj = J;
     stage_out(e, g, gout, e.vl, mem);
+  });
+}
+
+ga_status ga_deformation(ga_ctx* ctx, const void* v, void* u, void* detj, int mem) {
+  if (!ctx || !v || !u || !detj || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    auto* vin = stage_in(e, v, e.vl, mem, e.io_a);
+    T* uout = mem == GA_MEM_DEVICE ? static_cast<T*>(u) : e.io_b;
+    T* jout = mem == GA_MEM_DEVICE ? static_cast<T*>(detj) : e.tmp[1];
+    e.deformation(vin, uout, jout);
+    stage_out(e, u, uout, e.vl, mem);
+    stage_out(e, detj, jout, e.nv, mem);
   });
 }
 

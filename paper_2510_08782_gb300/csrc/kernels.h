@@ -86,6 +86,8 @@ cudaError_t launch_mismatch(const T* mT, const T* m1, T* lam, long long len, dou
 cudaError_t launch_sum_partials(const double* partial, int count, int nblocks, double* out, cudaStream_t st);
 // y = x + a s
 template <typename T>
+cudaError_t launch_fill(T* y, double value, long long len, cudaStream_t st);
+template <typename T>
 cudaError_t launch_axpy(T* y, const T* x, const T* s, double a, long long len, cudaStream_t st);
 // out = q + sum_i beta_i (q - v_i), beta on the device
 template <typename T>

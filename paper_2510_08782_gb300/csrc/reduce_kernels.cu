@@ -329,6 +329,19 @@ cudaError_t launch_sum_partials(const double* partial, int count, int nblocks, d
 }
 
 template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fill(T* __restrict__ y, T value, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    y[i] = value;
+}
+
+template <typename T>
+cudaError_t launch_fill(T* y, double value, long long len, cudaStream_t st) {
+  note_launches(1);
+  k_fill<T><<<grid_for(len), kThreads, 0, st>>>(y, (T)value, len);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_axpy(T* y, const T* x, const T* s, double a, long long len, cudaStream_t st) {
   note_launches(1);
   k_axpy<T><<<grid_for(len), kThreads, 0, st>>>(y, x, s, (T)a, len);
@@ -372,6 +385,7 @@ cudaError_t launch_gram_push(double* M, int ldm, int mkeep, const double* row, c
   template cudaError_t launch_mismatch<T>(const T*, const T*, T*, long long, double*, double*,        \
                                           cudaStream_t);                                              \
   template cudaError_t launch_axpy<T>(T*, const T*, const T*, double, long long, cudaStream_t);       \
+  template cudaError_t launch_fill<T>(T*, double, long long, cudaStream_t);                          \
   template cudaError_t launch_combine<T>(T*, const T*, const T* const*, const double*, int, long long, \
                                          cudaStream_t);
 GA_INST(float)

@@ -92,6 +92,7 @@ def test_null_arguments_rejected(libga):
     assert L.ga_objective(None, None, 0, ctypes.byref(out)) == 1
     assert L.ga_gradient(None, None, None, 0, None) == 1
     assert L.ga_step(None, None, 0, None) == 1
+    assert L.ga_deformation(None, None, None, None, 0) == 1
     assert L.ga_solve_batch(-1, None, None, 0, None) == 1
     assert L.ga_setup(None, None, None, None, 0, None, None) == 1
 
