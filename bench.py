@@ -158,6 +158,101 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Configuration sweep after the paper's studies: hyperparameters w and p = (sigma, tau) (Sec. 3.3),
+# regularisation parameter (Sec. 3.4) and mesh refinement with n_t proportional to n (Sec. 3.5).
+SWEEP_W = (1, 5, 10, 15, 20, 25, 50)
+SWEEP_P = ((1, 0), (5, 1), (1, 5), (5, 5), (4, 2), (2, 4), (6, 3), (3, 6))
+SWEEP_ALPHA = (1e-1, 5e-2, 1e-2, 5e-3, 1e-3, 5e-4)
+SWEEP_MESH = ((64, 4), (128, 8), (256, 16), (512, 32))
+
+
+def run_sweep(args):
+    """Solves of the 3D advection recipe (low-pass template of 256 signed blobs, |k| <= 4 velocity of
+    2 voxels, H2, FP32 fields) for every configuration of the three studies; one JSON line with a row
+    per solve: iterations, gradient/objective evaluations, PDE solves, relative mismatch (dist),
+    relative gradient and time to solution."""
+    import torch
+
+    import paper_2510_08782_gb300 as ga
+    from paper_2510_08782_gb300 import build
+    from synth.inputs import workload
+
+    build.build()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    parts = set(args.sweep_parts.split(","))
+    data = {}
+
+    def fields(n):
+        if n not in data:
+            w = workload("adv3d64", seed=0, n=(n, n, n))
+            data[n] = (torch.from_numpy(w["m0"].astype(np.float32)).cuda(),
+                       torch.from_numpy(w["m1"].astype(np.float32)).cuda())
+        return data[n]
+
+    def solve(n, nt, alpha, window, sigma, tau, rel_tol, method="ga-ngmres"):
+        m0, m1 = fields(n)
+        P = ga.Problem(m0, m1, nt=nt, model="advection", reg_order=2, alpha=alpha, prec="mixed", window=window,
+                       sigma=sigma, tau=tau, max_iter=200, rel_tol=rel_tol, method=method)
+        v = torch.zeros((3, n, n, n), dtype=torch.float32, device="cuda")
+        mis0 = P.objective(v)  # the regulariser vanishes at v = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        err = None
+        try:
+            st, _ = P.solve(v)
+        except ga.GaError as e:
+            err = str(e)
+            st = ga.Stats()
+            ga.lib().ga_get_stats(P.ctx, st)
+        torch.cuda.synchronize()
+        row = {"n": n, "nt": nt, "alpha": alpha, "w": window, "p": [sigma, tau], "method": method,
+               "iters": st.iters, "grad_evals": st.grad_evals, "obj_evals": st.obj_evals,
+               "pde_solves": st.pde_solves, "converged": bool(st.converged), "grad": st.rel_grad_inf,
+               "dist": st.mismatch / mis0 if mis0 > 0 else None, "tts_s": time.perf_counter() - t0,
+               "t_grad_ms": st.t_grad_ms, "t_obj_ms": st.t_obj_ms, "error": err}
+        P.close()
+        del v
+        return row
+
+    rows = {"hyper": [], "alpha": [], "mesh": []}
+    t_all = time.perf_counter()
+    tol = args.sweep_tol  # the paper's default tolerance is 5e-2 (Sec. 3.1)
+    if "hyper" in parts:  # Sec. 3.3: n = 128, n_t = 8, alpha = 1e-3
+        for w in SWEEP_W:
+            for sg, ta in SWEEP_P:
+                rows["hyper"].append(solve(128, 8, 1e-3, w, sg, ta, tol))
+        rows["hyper"].append(solve(128, 8, 1e-3, 0, 1, 0, tol, method="rpgd"))
+        rows["hyper"].append(solve(128, 8, 1e-3, 10, 4, 2, tol, method="ga-aa"))
+    if "alpha" in parts:  # Sec. 3.4
+        for a in SWEEP_ALPHA:
+            rows["alpha"].append(solve(128, 8, a, 0, 1, 0, tol, method="rpgd"))
+            for w in (10, 25):
+                for sg, ta in ((5, 1), (4, 2)):
+                    rows["alpha"].append(solve(128, 8, a, w, sg, ta, tol))
+    if "mesh" in parts:  # Sec. 3.5: w = 25, p = (4, 2), alpha = 1e-3, tolerance 1e-3
+        for n, nt in SWEEP_MESH:
+            if n > args.sweep_max_n:
+                continue
+            rows["mesh"].append(solve(n, nt, 1e-3, 25, 4, 2, 1e-3))
+            data.pop(n, None)
+            torch.cuda.empty_cache()
+    total_s = time.perf_counter() - t_all
+    if rank != 0:
+        return 0
+    allrows = rows["hyper"] + rows["alpha"] + rows["mesh"]
+    conv = sum(r["converged"] for r in allrows)
+    print(json.dumps({
+        "metric": "configuration sweep: iterations and time to rel-grad per configuration (3D advection, H2)",
+        "value": conv, "unit": "converged runs", "n_gpus": 1, "steps": len(allrows), "warmup": 0,
+        "ms_per_step": 1e3 * total_s / max(len(allrows), 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sweep: adv3d64 recipe; hyperparameters and alpha at 128^3 (n_t = 8), "
+                               "mesh 64..512 with n_t = n/16", "tol": args.sweep_tol, "mesh_tol": 1e-3},
+        "gpu_launches": ga.ga_kernel_launches(), "sweep": rows}))
+    return 0
+
+
 def run_batch(args):
     """Batched form: 32 independent 3D advection problems with grids drawn from {64,96,128,160}^3,
     n_t = 4, H1, alpha in {1e-2, 1e-3}, GA-NGMRES(5; 4, 2) to rel-grad 1e-2, FP32 fields. One step =
@@ -229,7 +324,12 @@ def main():
     ap.add_argument("--no-tts", action="store_true")
     ap.add_argument("--prof-class", type=int, default=PROF_SL_FWD)
     ap.add_argument("--grid", type=int, default=N, help="grid size (default 256; smaller only for smoke runs)")
-    ap.add_argument("--workload", default="cont3d256", choices=["cont3d256", "batch"],
+    ap.add_argument("--sweep-parts", default="hyper,alpha,mesh",
+                    help="--workload sweep: comma-separated subset of hyper, alpha, mesh")
+    ap.add_argument("--sweep-max-n", type=int, default=512, help="--workload sweep: largest mesh")
+    ap.add_argument("--sweep-tol", type=float, default=5e-2,
+                    help="--workload sweep: tolerance of the hyperparameter and alpha parts (mesh: 1e-3)")
+    ap.add_argument("--workload", default="cont3d256", choices=["cont3d256", "batch", "sweep"],
                     help="cont3d256 (default) or batch: 32 independent advection problems of uneven size")
     ap.add_argument("--compare-methods", action="store_true",
                     help="also time the same solve with GA-AA and RPGD (mixed precision, same settings)")
@@ -242,6 +342,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
 
     import torch
 

@@ -70,7 +70,7 @@ typedef struct {
 
 /* Solver options (Alg. 3 inputs, line search of Sec. 2.3). */
 typedef struct {
-  int window;          /* w >= 0 (at most 30)                                               */
+  int window;          /* w >= 0 (at most 62)                                               */
   int sigma;           /* NGMRES steps per period, >= 1                                     */
   int tau;             /* fixed-point steps per period, >= 0                                */
   int max_iter;        /* n_iter > 0                                                        */

@@ -58,14 +58,14 @@ ga_status ga_op_apply_L(ga_ctx* ctx, const void* v, void* Lv);
 ga_status ga_op_leray(ga_ctx* ctx, const void* v, void* pv);
 
 /* FP64 compensated inner products out[i] = sum_j a[j] * b_i[j] over len elements of the
- * context element type, for i < count (count <= 32). b: device array of count device pointers
+ * context element type, for i < count (count <= 64). b: device array of count device pointers
  * held in HOST memory (the pointer list itself is host memory); out: host memory. */
 ga_status ga_op_dots(ga_ctx* ctx, const void* a, const void* const* b, int count, size_t len,
                      double* out);
 
 /* NGMRES least squares on the device (Alg. 1, "arg min" line) from its FP64 Gram data:
  * beta = argmin || g_q + sum_i beta_i (g_q - g_i) ||_2, given c = <g_q, g_q>, a_i = <g_q, g_i>
- * and M_ij = <g_i, g_j> for i, j < m (m <= 31). Truncated symmetric eigen-solve of the normal
+ * and M_ij = <g_i, g_j> for i, j < m (m <= 63). Truncated symmetric eigen-solve of the normal
  * equations, dropping eigenvalues below 1e-14 * max. All arrays in HOST memory. */
 ga_status ga_op_lsq(ga_ctx* ctx, int m, double c, const double* a, const double* M, double* beta);
 

@@ -40,7 +40,9 @@ void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); 
 
 namespace {
 
-constexpr int kNumRes = 64;  // device FP64 result slots
+constexpr int kNumRes = 128;                // device FP64 result slots
+constexpr int kResDots = 16;                // first slot of the window inner products
+constexpr int kResLsq = kResDots + kMaxDots;  // least-squares diagnostics
 
 struct Fail {
   ga_status st;
@@ -92,6 +94,7 @@ template <typename T> struct Engine : EngineBase {
 
   T *m0 = nullptr, *m1 = nullptr, *xm = nullptr, *xp = nullptr, *mu = nullptr;
   T *lam[2] = {nullptr, nullptr}, *body = nullptr, *tmp[2] = {nullptr, nullptr};
+  T* wtmp = nullptr;  // alpha L v for calls that do not carry it
   T *states = nullptr, *seg = nullptr, *io_a = nullptr, *io_b = nullptr;
   int nslots = 0, seg_base = -1;
   cx<T> *vh = nullptr, *bh = nullptr;
@@ -212,13 +215,15 @@ template <typename T> struct Engine : EngineBase {
     ck(cudaMallocHost(&pinned, sizeof(double) * kNumRes), "cudaMallocHost");
     hres = static_cast<double*>(pinned);
 
-    // solver pools: window (w+1) + trial q + one more, for iterates and gradients
+    // solver pools: window (w+1) + trial q + one more, for iterates and gradients. An iterate buffer
+    // holds v in [0, vl) and w = alpha L v in [vl, 2 vl); S holds s and alpha L s the same way.
     W1 = c->opts.window + 1;
     for (int i = 0; i < W1 + 2; ++i) {
-      vfree.push_back(dalloc<T>(vl));
+      vfree.push_back(dalloc<T>(2 * vl));
       gfree.push_back(dalloc<T>(vl));
     }
-    S = dalloc<T>(vl);
+    S = dalloc<T>(2 * vl);
+    wtmp = dalloc<T>(vl);
     dM = dalloc<double>((long long)W1 * W1);
     dbeta = dalloc<double>(kMaxWin + 4);
     ck(cudaMemsetAsync(dM, 0, sizeof(double) * W1 * W1, st), "memset");
@@ -291,12 +296,37 @@ template <typename T> struct Engine : EngineBase {
   bool needs_mu_adjoint() const { return model != GA_MODEL_CONTINUITY; }
 
   // F v into vh and the regulariser sum into dres[slot]
-  void prologue(const T* v, int res_slot) {
+  // w = alpha L v by the transform (Sec. 2.2): used where w is not carried along with v.
+  void apply_alphaL(const T* v, T* w) {
     for (int c = 0; c < dim; ++c) r2c(v + c * nv, vh + c * g.nhalf);
-    ck(launch_reg_sum<T>(g, s, vh, dpart, st), "reg_sum");
-    ck(launch_sum_partials(dpart, 1, kRedBlocks, dres + res_slot, st), "sum");
+    SpecArgs sa{SPEC_APPLY_ALPHA_L, s, alpha, 0, 0};
+    ck(launch_spectral<T>(g, sa, vh, nullptr, st), "spectral alpha L");
+    for (int c = 0; c < dim; ++c) c2r(vh + c * g.nhalf, w + c * nv);
   }
-  double reg_value(double raw) const { return 0.5 * alpha * hd / (double)nv * raw; }
+  // sum_x v . w into dres[slot]; the regulariser (alpha/2) <v, L v> is h^d/2 times it for w = alpha L v.
+  void reg_dot(const T* v, const T* w, int slot) {
+    const T* bl[1] = {w};
+    ck(launch_dots<T>(v, bl, 1, vl, dpart, dres + slot, st), "regulariser dot");
+  }
+  double reg_value(double raw) const { return 0.5 * hd * raw; }
+
+  // s = -(alpha L)^{-1} (P) g (Eq. (9)) into sout and, when tout != nullptr, t = alpha L s into tout.
+  // Advection/continuity: alpha L^ s^ = -g^ for k != 0 and 0 at k = 0, so t = -(g - mean g) in real
+  // space. Incompressible: t^ = alpha L^ s^ by the transform.
+  void precond_into(const T* gin, T* sout, T* tout) {
+    for (int c = 0; c < dim; ++c) r2c(gin + c * nv, bh + c * g.nhalf);
+    const bool inc = model == GA_MODEL_INCOMPRESSIBLE;
+    if (tout && !inc) ck(launch_neg_centered<T>(g, gin, bh, tout, st), "alpha L s");
+    SpecArgs sa{SPEC_PRECOND, s, alpha, inc ? 1 : 0, 0};
+    ck(launch_spectral<T>(g, sa, bh, nullptr, st), "spectral precond");
+    if (tout && inc) {
+      ck(cudaMemcpyAsync(vh, bh, sizeof(cx<T>) * g.nhalf * dim, cudaMemcpyDeviceToDevice, st), "copy s^");
+      SpecArgs sl{SPEC_APPLY_ALPHA_L, s, alpha, 0, 0};
+      ck(launch_spectral<T>(g, sl, vh, nullptr, st), "spectral alpha L s");
+      for (int c = 0; c < dim; ++c) c2r(vh + c * g.nhalf, tout + c * nv);
+    }
+    for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, sout + c * nv);
+  }
 
   // State solve keeping only the final state; returns pointer to m(1).
   const T* forward_final(const T* v) {
@@ -345,10 +375,15 @@ template <typename T> struct Engine : EngineBase {
   // obj(v): one state solve. Results: dres[0] = sum (m(1) - m1)^2, dres[1] = regulariser sum.
   // With keep = true the state solve stores its trajectory (and v^, mu, X-) so that an immediately
   // following gradient(v) on the same, unmodified buffer reuses them instead of solving again.
-  double objective(const T* v, double* mismatch = nullptr, bool keep = false) {
+  // w = alpha L v when the caller carries it (the solver), else nullptr (computed by the transform).
+  double objective(const T* v, double* mismatch = nullptr, bool keep = false, const T* w = nullptr) {
     fwd_cache = nullptr;
     ck(cudaEventRecord(ev[0], st), "event");
-    prologue(v, 1);
+    if (!w) {
+      apply_alphaL(v, wtmp);
+      w = wtmp;
+    }
+    reg_dot(v, w, 1);
     if (needs_mu_forward() || keep) compute_mu(v);
     const T* mT;
     if (keep) {
@@ -371,7 +406,7 @@ template <typename T> struct Engine : EngineBase {
     if (keep) fwd_cache = v;
     return m + reg_value(hres[1]);
   }
-  const T* fwd_cache = nullptr;  // v whose trajectory, v^, mu and X- are current (see objective)
+  const T* fwd_cache = nullptr;  // v whose trajectory, mu and X- are current (see objective)
 
   // Body force b (not projected) from the adjoint started at lam_init (lam_init may be lam[0]).
   // Requires departure points, mu and the forward states.
@@ -397,28 +432,37 @@ template <typename T> struct Engine : EngineBase {
     }
   }
 
-  // Reduced gradient; writes g (vl) and, when s_out != nullptr, s = -(alpha L)^{-1} (P) g.
-  double gradient(const T* v, T* gout, T* s_out, double* mismatch = nullptr) {
+  // Reduced gradient g = alpha L v + (P) b (Eq. (3)) into gout (vl). w = alpha L v: carried by the
+  // solver through every linear update of v, so the regulariser term never passes through a transform
+  // of v whose rounding the symbol |k|^{2s} would amplify; nullptr computes it by the transform. When
+  // s_out != nullptr, writes s = -(alpha L)^{-1} (P) g to s_out and alpha L s to s_out + vl.
+  double gradient(const T* v, T* gout, T* s_out, double* mismatch = nullptr, const T* w = nullptr) {
     ck(cudaEventRecord(ev[0], st), "event");
     const bool reuse = fwd_cache == v;  // trajectory of the last objective(v, .., keep) call
     fwd_cache = nullptr;
+    if (!w) {
+      apply_alphaL(v, wtmp);
+      w = wtmp;
+    }
+    reg_dot(v, w, 1);
     if (reuse) {
-      // v^, its regulariser sum, mu, X- and the stored states are those of v: only X+ is missing
+      // mu, X- and the stored states are those of v: only X+ is missing
       ck(launch_departure<T>(g, v, xp, xm, (T)(-ht), st, /*both=*/0), "departure");
     } else {
-      prologue(v, 1);
       compute_mu(v);
       ck(launch_departure<T>(g, v, xm, xp, (T)ht, st), "departure");
       forward_all();
     }
     ck(launch_mismatch<T>(slot(nt), m1, lam[0], nv, dpart, dres, st), "mismatch");
     body_force(lam[0]);
-    for (int c = 0; c < dim; ++c) r2c(body + c * nv, bh + c * g.nhalf);
-    SpecArgs sa{SPEC_EPILOGUE, s, alpha, model == GA_MODEL_INCOMPRESSIBLE ? 1 : 0, s_out ? 1 : 0};
-    ck(launch_spectral<T>(g, sa, bh, vh, st), "spectral epilogue");
-    for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, gout + c * nv);
-    if (s_out)
-      for (int c = 0; c < dim; ++c) c2r(vh + c * g.nhalf, s_out + c * nv);
+    if (model == GA_MODEL_INCOMPRESSIBLE) {  // P b by the transform, in place
+      for (int c = 0; c < dim; ++c) r2c(body + c * nv, bh + c * g.nhalf);
+      SpecArgs sp{SPEC_LERAY, s, alpha, 1, 0};
+      ck(launch_spectral<T>(g, sp, bh, nullptr, st), "spectral leray");
+      for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, body + c * nv);
+    }
+    ck(launch_axpy<T>(gout, body, w, 1.0, vl, st), "g = (P) b + w");
+    if (s_out) precond_into(gout, s_out, s_out + vl);
     ck(launch_maxabs<T>(gout, vl, dpart, dres + 2, st), "maxabs");
     ck(cudaEventRecord(ev[1], st), "event");
     read_results(3);
@@ -440,12 +484,8 @@ template <typename T> struct Engine : EngineBase {
   double last_ginf = 0.0;
 
   void precond(const T* gin, T* sout) {
-    for (int c = 0; c < dim; ++c) r2c(gin + c * nv, bh + c * g.nhalf);
-    SpecArgs sa{SPEC_PRECOND, s, alpha, model == GA_MODEL_INCOMPRESSIBLE ? 1 : 0, 0};
-    ck(launch_spectral<T>(g, sa, bh, nullptr, st), "spectral precond");
-    for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, sout + c * nv);
+    precond_into(gin, sout, nullptr);
   }
-
   double dot_l2(const T* a, const T* b) {
     const T* bl[1] = {b};
     ck(launch_dots<T>(a, bl, 1, vl, dpart, dres + 8, st), "dots");
@@ -521,8 +561,8 @@ template <typename T> struct Engine : EngineBase {
     std::vector<const T*> bl;
     bl.push_back(gv);
     for (int i = 0; i < keep; ++i) bl.push_back(win[i].second);
-    ck(launch_dots<T>(gv, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "window dots");
-    ck(launch_gram_push(dM, W1, keep, dres + 16, st), "gram push");
+    ck(launch_dots<T>(gv, bl.data(), (int)bl.size(), vl, dpart, dres + kResDots, st), "window dots");
+    ck(launch_gram_push(dM, W1, keep, dres + kResDots, st), "gram push");
     win.push_front({v, gv});
   }
 
@@ -552,8 +592,8 @@ template <typename T> struct Engine : EngineBase {
     std::vector<const T*> bl;
     bl.push_back(r);
     for (int i = 0; i < keep; ++i) bl.push_back(awin[i].second);
-    ck(launch_dots<T>(r, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "window dots");
-    ck(launch_gram_push(dM, W1, keep, dres + 16, st), "gram push");
+    ck(launch_dots<T>(r, bl.data(), (int)bl.size(), vl, dpart, dres + kResDots, st), "window dots");
+    ck(launch_gram_push(dM, W1, keep, dres + kResDots, st), "gram push");
     awin.push_front({q, r});
   }
 
@@ -569,7 +609,8 @@ template <typename T> struct Engine : EngineBase {
     T* v = take(vfree);
     T* gv = take(gfree);
     ck(cudaMemcpyAsync(v, v0, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy v0");
-    J = gradient(v, gv, S, &mis);
+    apply_alphaL(v, v + vl);  // from here on w = alpha L v follows every linear update of v
+    J = gradient(v, gv, S, &mis, v + vl);
     s_valid = true;
     g0inf = last_ginf;
     if (aa()) {
@@ -593,14 +634,14 @@ template <typename T> struct Engine : EngineBase {
   T* qmap(const T* v, const T* gv) {
     const ga_solver_opts& o = ctx->opts;
     ga_stats& stt = ctx->stats;
-    if (!s_valid) precond(gv, S);
+    if (!s_valid) precond_into(gv, S, S + vl);
     const double gs = dot_l2(gv, S);
     T* q = take(vfree);
     double rho = rho_mem, Jq = 0.0;
     bool ok = false;
     for (int it = 0; it <= o.max_backtracks; ++it) {
-      ck(launch_axpy<T>(q, v, S, rho, vl, st), "axpy");
-      Jq = objective(q, nullptr, /*keep=*/true);
+      ck(launch_axpy<T>(q, v, S, rho, 2 * vl, st), "axpy");  // q = v + rho s and alpha L q
+      Jq = objective(q, nullptr, /*keep=*/true, q + vl);
       stt.ls_trials += 1;
       if (Jq < J + o.armijo_c * rho * gs) {
         rho_mem = (it == 0) ? 2.0 * rho : rho;
@@ -647,11 +688,11 @@ template <typename T> struct Engine : EngineBase {
     T *vn, *gn = take(gfree);
     double Jn, misn;
     if (fp) {
-      Jn = gradient(q, gn, S, &misn);  // reuses the accepted trial's state trajectory
+      Jn = gradient(q, gn, S, &misn, q + vl);  // reuses the accepted trial's state trajectory
       vn = q;
       if (W1 > 1) {
         T* qw = take(vfree);
-        ck(cudaMemcpyAsync(qw, q, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy q");
+        ck(cudaMemcpyAsync(qw, q, sizeof(T) * 2 * vl, cudaMemcpyDeviceToDevice, st), "copy q");
         push_aa(qw, r);
       } else {
         gfree.push_back(r);
@@ -661,14 +702,14 @@ template <typename T> struct Engine : EngineBase {
       std::vector<const T*> bl;
       bl.push_back(r);
       for (int i = 0; i < m; ++i) bl.push_back(awin[i].second);
-      ck(launch_dots<T>(r, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "lsq dots");
-      ck(launch_lsq(m, dres + 16, dM, W1, dbeta, dres + 56, st), "lsq");
+      ck(launch_dots<T>(r, bl.data(), (int)bl.size(), vl, dpart, dres + kResDots, st), "lsq dots");
+      ck(launch_lsq(m, dres + kResDots, dM, W1, dbeta, dres + kResLsq, st), "lsq");
       vn = take(vfree);
       std::vector<const T*> qlst;
       for (int i = 0; i < m; ++i) qlst.push_back(awin[i].first);
-      ck(launch_combine<T>(vn, q, qlst.data(), dbeta, m, vl, st), "combine");
+      ck(launch_combine<T>(vn, q, qlst.data(), dbeta, m, 2 * vl, st), "combine");  // v and alpha L v
       push_aa(q, r);  // stream order keeps a dropped entry intact until the combination has read it
-      Jn = gradient(vn, gn, S, &misn);
+      Jn = gradient(vn, gn, S, &misn, vn + vl);
     }
     vfree.push_back(cur_v);
     gfree.push_back(cur_g);
@@ -692,26 +733,26 @@ template <typename T> struct Engine : EngineBase {
     T *vn, *gn;
     double Jn, misn;
     if (fp) {
-      Jn = gradient(q, gq, S, &misn);
+      Jn = gradient(q, gq, S, &misn, q + vl);
       vn = q;
       gn = gq;
     } else {
       double misq;
-      gradient(q, gq, nullptr, &misq);
+      gradient(q, gq, nullptr, &misq, q + vl);
       const int m = (int)win.size();  // w^(k) + 1 window entries
       std::vector<const T*> bl;
       bl.push_back(gq);
       for (int i = 0; i < m; ++i) bl.push_back(win[i].second);
-      ck(launch_dots<T>(gq, bl.data(), (int)bl.size(), vl, dpart, dres + 16, st), "lsq dots");
-      ck(launch_lsq(m, dres + 16, dM, W1, dbeta, dres + 56, st), "lsq");
+      ck(launch_dots<T>(gq, bl.data(), (int)bl.size(), vl, dpart, dres + kResDots, st), "lsq dots");
+      ck(launch_lsq(m, dres + kResDots, dM, W1, dbeta, dres + kResLsq, st), "lsq");
       vn = take(vfree);
       std::vector<const T*> vlst;
       for (int i = 0; i < m; ++i) vlst.push_back(win[i].first);
-      ck(launch_combine<T>(vn, q, vlst.data(), dbeta, m, vl, st), "combine");
+      ck(launch_combine<T>(vn, q, vlst.data(), dbeta, m, 2 * vl, st), "combine");  // v and alpha L v
       vfree.push_back(q);
       gfree.push_back(gq);
       gn = take(gfree);
-      Jn = gradient(vn, gn, S, &misn);
+      Jn = gradient(vn, gn, S, &misn, vn + vl);
     }
     push_window(vn, gn);
     finish_step(fp, Jn, misn);
@@ -1117,10 +1158,10 @@ ga_status ga_op_dots(ga_ctx* ctx, const void* a, const void* const* b, int count
     using T = typename std::remove_reference<decltype(*e.m0)>::type;
     std::vector<const T*> bl(count);
     for (int i = 0; i < count; ++i) bl[i] = static_cast<const T*>(b[i]);
-    e.ck(launch_dots<T>(static_cast<const T*>(a), bl.data(), count, (long long)len, e.dpart, e.dres + 16, e.st),
+    e.ck(launch_dots<T>(static_cast<const T*>(a), bl.data(), count, (long long)len, e.dpart, e.dres + kResDots, e.st),
          "dots");
-    e.read_results(16 + count);
-    for (int i = 0; i < count; ++i) out[i] = e.hres[16 + i];
+    e.read_results(kResDots + count);
+    for (int i = 0; i < count; ++i) out[i] = e.hres[kResDots + i];
   });
 }
 

@@ -10,8 +10,8 @@ namespace ga {
 
 constexpr int kThreads = 256;       // threads per CTA of the streaming kernels
 constexpr int kRedBlocks = 152 * 4; // CTAs of the reduction kernels (4 per SM of a GB300)
-constexpr int kMaxDots = 32;        // vectors per multi-dot call
-constexpr int kMaxWin = 31;         // window entries in the least-squares kernel
+constexpr int kMaxDots = 64;        // vectors per multi-dot call
+constexpr int kMaxWin = 63;         // window entries in the least-squares kernel
 
 template <typename T> struct PtrList { const T* p[16]; };
 
@@ -38,7 +38,7 @@ template <typename T>
 cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, cudaStream_t st);
 
 // ---- pointwise spectral operators (spectral_kernels.cu) --------------------------------------
-enum SpecMode { SPEC_APPLY_L = 0, SPEC_LERAY = 1, SPEC_PRECOND = 2, SPEC_EPILOGUE = 3 };
+enum SpecMode { SPEC_APPLY_L = 0, SPEC_LERAY = 1, SPEC_PRECOND = 2, SPEC_EPILOGUE = 3, SPEC_APPLY_ALPHA_L = 4 };
 struct SpecArgs {
   int mode;
   int s;            // regulariser order
@@ -51,6 +51,10 @@ struct SpecArgs {
 template <typename T>
 cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cx<T>* v, cudaStream_t st);
 // partial[b] = sum over the half spectrum (weights 1/2) of |k|^{2s} |v^_c|^2 summed over c.
+// t = -(g - mean(g)) per component (= alpha L s for s = -(alpha L)^{-1} g), the means taken from the
+// zero modes of gh, the half spectrum of g
+template <typename T>
+cudaError_t launch_neg_centered(const Grid& g, const T* gv, const cx<T>* gh, T* t, cudaStream_t st);
 template <typename T>
 cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partial, cudaStream_t st);
 

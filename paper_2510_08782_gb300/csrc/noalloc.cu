@@ -19,10 +19,11 @@
 #include "../../include/ga_ops.h"
 #include "kernels.h"
 
-// Room for the per-CTA partial sums of up to kMaxDots inner products: kMaxDots * kRedBlocks
+// Room for the per-CTA partial sums of up to kNoAllocDots inner products: kNoAllocDots * kRedBlocks
 // doubles = 32 * 608 * 8 bytes = 155,648 bytes, held on every device that loads the library until
 // the process exits.
-static __device__ __align__(256) double g_dot_scratch[ga::kMaxDots * ga::kRedBlocks];
+constexpr int kNoAllocDots = 32;
+static __device__ __align__(256) double g_dot_scratch[kNoAllocDots * ga::kRedBlocks];
 
 namespace {
 
@@ -57,7 +58,7 @@ extern "C" ga_status ga_dots_noalloc(int prec, const void* a, const void* const*
     ga::set_global_error("ga_dots_noalloc: null pointer, empty vectors or unknown precision");
     return GA_ERR_ARG;
   }
-  if (count < 1 || count > ga::kMaxDots) {
+  if (count < 1 || count > kNoAllocDots) {
     ga::set_global_error("ga_dots_noalloc: count must be between 1 and 32 (the size of the fixed scratch array)");
     return GA_ERR_ARG;
   }

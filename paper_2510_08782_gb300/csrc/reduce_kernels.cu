@@ -11,6 +11,8 @@
 // are diagonalised by cyclic Jacobi rotations in FP64 and eigenvalues below 1e-14 max are dropped.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kernels.h"
 
 namespace ga {
@@ -132,7 +134,7 @@ k_mismatch(const T* __restrict__ mT, const T* __restrict__ m1, T* __restrict__ l
 // strided subset in FP64 (Neumaier), then a fixed shuffle tree; deterministic.
 __global__ void k_sum_partials(const double* __restrict__ partial, int count, int nblocks,
                                double* __restrict__ out) {
-  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= count) return;
   double s = 0.0, c = 0.0;
   for (int b = lane; b < nblocks; b += 32) {
@@ -185,35 +187,53 @@ k_combine(T* __restrict__ out, const T* __restrict__ q, PtrList<T> v, const doub
   }
 }
 
-// Cyclic Jacobi eigen-solve of the m x m normal equations, one thread (m <= kMaxWin).
-__global__ void k_lsq(int m, const double* __restrict__ dots, const double* __restrict__ M, int ldm,
-                      double* __restrict__ beta, double* __restrict__ info) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double G[kMaxWin * kMaxWin];
-  double U[kMaxWin * kMaxWin];
-  double r[kMaxWin];
+// Cyclic Jacobi eigen-solve of the m x m normal equations (m <= kMaxWin) by one warp, with G, U and
+// the right-hand side in shared memory. The rotations are applied one after another; the lanes share
+// the row, column and eigenvector updates of each rotation. Every element receives the same
+// operations in the same order as in a one-thread loop, and the scalar sums are taken by lane 0, so
+// the result does not depend on the warp width.
+__global__ void __launch_bounds__(32) k_lsq(int m, const double* __restrict__ dots, const double* __restrict__ M,
+                                            int ldm, double* __restrict__ beta, double* __restrict__ info) {
+  extern __shared__ double sh[];
+  double* G = sh;              // m * m
+  double* U = sh + m * m;      // m * m
+  double* r = sh + 2 * m * m;  // m
+  __shared__ double s_scal[2];  // off-diagonal mass, Frobenius norm
+  __shared__ int s_stop;
+  const int lane = threadIdx.x;
   const double c = dots[0];
-  for (int i = 0; i < m; ++i) {
-    r[i] = c - dots[1 + i];
-    for (int j = 0; j < m; ++j) {
-      G[i * m + j] = c - dots[1 + i] - dots[1 + j] + M[i * ldm + j];
-      U[i * m + j] = (i == j) ? 1.0 : 0.0;
-    }
+  for (int e = lane; e < m * m; e += 32) {
+    const int i = e / m, j = e % m;
+    G[e] = c - dots[1 + i] - dots[1 + j] + M[i * ldm + j];
+    U[e] = (i == j) ? 1.0 : 0.0;
   }
-  for (int i = 0; i < m; ++i)  // symmetrise against rounding of the expansion
-    for (int j = i + 1; j < m; ++j) {
+  for (int i = lane; i < m; i += 32) r[i] = c - dots[1 + i];
+  __syncwarp();
+  for (int e = lane; e < m * m; e += 32) {  // symmetrise against rounding of the expansion
+    const int i = e / m, j = e % m;
+    if (j > i) {
       const double s = 0.5 * (G[i * m + j] + G[j * m + i]);
       G[i * m + j] = s;
       G[j * m + i] = s;
     }
-  double fro = 0.0;
-  for (int i = 0; i < m * m; ++i) fro += G[i] * G[i];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double fro = 0.0;
+    for (int i = 0; i < m * m; ++i) fro += G[i] * G[i];
+    s_scal[1] = fro;
+  }
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = i + 1; j < m; ++j) off += 2.0 * G[i * m + j] * G[i * m + j];
-    if (off <= 1e-30 * fro || off == 0.0) break;
+    __syncwarp();
+    if (lane == 0) {
+      double off = 0.0;
+      for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j) off += 2.0 * G[i * m + j] * G[i * m + j];
+      s_stop = (off <= 1e-30 * s_scal[1] || off == 0.0) ? 1 : 0;
+    }
+    __syncwarp();
+    if (s_stop) break;
     for (int p = 0; p < m; ++p)
       for (int q = p + 1; q < m; ++q) {
         const double apq = G[p * m + q];
@@ -222,23 +242,28 @@ __global__ void k_lsq(int m, const double* __restrict__ dots, const double* __re
         const double theta = (aqq - app) / (2.0 * apq);
         const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
         const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-        for (int k = 0; k < m; ++k) {  // G <- J^T G J
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) {  // G <- J^T G J, columns first
           const double gkp = G[k * m + p], gkq = G[k * m + q];
           G[k * m + p] = cs * gkp - sn * gkq;
           G[k * m + q] = sn * gkp + cs * gkq;
         }
-        for (int k = 0; k < m; ++k) {
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) {
           const double gpk = G[p * m + k], gqk = G[q * m + k];
           G[p * m + k] = cs * gpk - sn * gqk;
           G[q * m + k] = sn * gpk + cs * gqk;
         }
-        for (int k = 0; k < m; ++k) {  // U <- U J
+        for (int k = lane; k < m; k += 32) {  // U <- U J
           const double ukp = U[k * m + p], ukq = U[k * m + q];
           U[k * m + p] = cs * ukp - sn * ukq;
           U[k * m + q] = sn * ukp + cs * ukq;
         }
+        __syncwarp();
       }
   }
+  __syncwarp();
+  if (lane != 0) return;
   double lmax = 0.0;
   for (int i = 0; i < m; ++i) lmax = fmax(lmax, G[i * m + i]);
   const double thr = 1e-14 * lmax;
@@ -299,7 +324,8 @@ cudaError_t launch_dots(const T* a, const T* const* b, int count, long long len,
     if (e != cudaSuccess) return e;
   }
   note_launches(1);
-  k_sum_partials<<<1, 32 * count, 0, st>>>(partial, count, kRedBlocks, out);
+  // one warp per product, at most 32 warps per block
+  k_sum_partials<<<(count + 31) / 32, 32 * (count < 32 ? count : 32), 0, st>>>(partial, count, kRedBlocks, out);
   return cudaGetLastError();
 }
 
@@ -367,8 +393,15 @@ cudaError_t launch_combine(T* out, const T* q, const T* const* v, const double* 
 cudaError_t launch_lsq(int m, const double* dots, const double* M, int ldm, double* beta, double* info,
                        cudaStream_t st) {
   if (m < 1 || m > kMaxWin) return cudaErrorInvalidValue;
+  constexpr size_t kMaxSmem = sizeof(double) * (2 * kMaxWin * kMaxWin + kMaxWin);
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {  // one process-wide setting, the largest size any call needs
+    cudaError_t e = cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    if (e != cudaSuccess) return e;
+    attr.store(true);
+  }
   note_launches(1);
-  k_lsq<<<1, 32, 0, st>>>(m, dots, M, ldm, beta, info);
+  k_lsq<<<1, 32, sizeof(double) * (2 * m * m + m), st>>>(m, dots, M, ldm, beta, info);
   return cudaGetLastError();
 }
 

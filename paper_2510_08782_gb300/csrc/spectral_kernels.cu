@@ -76,8 +76,9 @@ k_spectral(Grid g, SpecArgs a, cx<T>* __restrict__ x, cx<T>* __restrict__ v) {
     const T L = symbol_L<T>(kv, a.s);
     cx<T> xv[3];
     for (int c = 0; c < dim; ++c) xv[c] = x[c * nh + idx];
-    if (a.mode == SPEC_APPLY_L) {
-      for (int c = 0; c < dim; ++c) x[c * nh + idx] = cscale(xv[c], (T)L);
+    if (a.mode == SPEC_APPLY_L || a.mode == SPEC_APPLY_ALPHA_L) {
+      const T f = a.mode == SPEC_APPLY_L ? (T)L : (T)(a.alpha * L);
+      for (int c = 0; c < dim; ++c) x[c * nh + idx] = cscale(xv[c], f);
       continue;
     }
     if (a.mode == SPEC_LERAY) {
@@ -104,6 +105,19 @@ k_spectral(Grid g, SpecArgs a, cx<T>* __restrict__ x, cx<T>* __restrict__ v) {
       if (a.project) leray<T>(kv, dim, gv);
       for (int c = 0; c < dim; ++c) v[c * nh + idx] = cscale(gv[c], (T)inv);
     }
+  }
+}
+
+// t = alpha L s for s = -(alpha L)^{-1} g (Eq. (9)): alpha L^ s^ = -g^ wherever L^ != 0 and 0 at k = 0,
+// so t_c = -(g_c - mean(g_c)), the mean read from the zero mode gh_c(0) = sum(g_c).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_neg_centered(const T* __restrict__ gv, const cx<T>* __restrict__ gh, T* __restrict__ t, long long nv, long long nh,
+               int dim) {
+  for (int c = 0; c < dim; ++c) {
+    const T mean = gh[c * nh].x / (T)nv;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
+      t[c * nv + i] = -(gv[c * nv + i] - mean);
   }
 }
 
@@ -161,9 +175,20 @@ cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partia
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_neg_centered(const Grid& g, const T* gv, const cx<T>* gh, T* t, cudaStream_t st) {
+  long long blocks = (g.nvox + kThreads - 1) / kThreads;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  note_launches(1);
+  k_neg_centered<T><<<(unsigned)blocks, kThreads, 0, st>>>(gv, gh, t, g.nvox, g.nhalf, g.dim);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_spectral<float>(const Grid&, const SpecArgs&, cx<float>*, cx<float>*, cudaStream_t);
 template cudaError_t launch_spectral<double>(const Grid&, const SpecArgs&, cx<double>*, cx<double>*, cudaStream_t);
 template cudaError_t launch_reg_sum<float>(const Grid&, int, const cx<float>*, double*, cudaStream_t);
 template cudaError_t launch_reg_sum<double>(const Grid&, int, const cx<double>*, double*, cudaStream_t);
+template cudaError_t launch_neg_centered<float>(const Grid&, const float*, const cx<float>*, float*, cudaStream_t);
+template cudaError_t launch_neg_centered<double>(const Grid&, const double*, const cx<double>*, double*, cudaStream_t);
 
 }  // namespace ga

@@ -73,7 +73,7 @@ def test_setup_rejects_bad_descriptors(libga, bad):
     assert "invalid" in libga.ga_last_error(None)
 
 
-@pytest.mark.parametrize("bad", [dict(window=40), dict(sigma=0), dict(tau=-1), dict(max_iter=0),
+@pytest.mark.parametrize("bad", [dict(window=63), dict(sigma=0), dict(tau=-1), dict(max_iter=0),
                                  dict(variant=3), dict(armijo_c=0.0), dict(method=5)])
 def test_setup_rejects_bad_options(libga, bad):
     d, o = _desc(libga)

@@ -73,6 +73,32 @@ def test_spectral_derivative_and_divergence(shape, prec):
     assert rel_l2(host(mu), osp.div(v)) < TOL[prec] * 10
 
 
+LONG_AXES = [(4, 8, 512), (4, 512, 8), (512, 4, 8), (6, 10, 384), (4, 480, 6), (1024, 4, 4)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", LONG_AXES)
+def test_fft_and_derivatives_on_long_axes(shape, prec):
+    """Transform lengths beyond the compiled plans (384, 480, 512, 1024) along every axis: R2C/C2R and
+    the fused derivative passes against numpy."""
+    import paper_2510_08782_gb300 as ga
+
+    P, _, _, _ = _problem(shape, prec)
+    f = quantise(random_fourier_field(shape, 1, 9, np.random.default_rng(3))[0], prec)
+    fh = empty(shape[:-1] + (shape[-1] // 2 + 1, 2), prec)
+    ga.ga_op_fft_r2c(P.ctx, P.dtype, to_dev(f, prec), fh)
+    ref = np.fft.rfftn(f)
+    assert rel_l2(host(fh), np.stack([ref.real, ref.imag], axis=-1)) < TOL[prec]
+    back = empty(shape, prec)
+    ga.ga_op_fft_c2r(P.ctx, P.dtype, fh, back)
+    assert rel_l2(host(back), f) < TOL[prec]
+    gref = osp.grad(f)
+    for a in range(3):
+        out = empty(shape, prec)
+        ga.ga_op_deriv(P.ctx, P.dtype, to_dev(f, prec), a, out)
+        assert rel_l2(host(out), gref[a]) < TOL[prec] * 4, (a, rel_l2(host(out), gref[a]))
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("s", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(32, 24), (16, 12, 20)])
@@ -177,6 +203,27 @@ def test_dots_and_lsq(prec):
     M = np.array([[gi @ gj for gj in gw] for gi in gw])
     beta = ga.ga_op_lsq(P.ctx, c, a, M)
     np.testing.assert_allclose(beta, ngmres_lsq(gq, gw), rtol=1e-9, atol=1e-12)
+
+
+def test_dots_and_lsq_at_the_largest_window():
+    """w = 62: 64 inner products in one call and the 63-entry least-squares solve (the sizes the paper's
+    w = 50 runs need), against exact products and the oracle's lstsq on the explicit differences."""
+    import paper_2510_08782_gb300 as ga
+    from oracle.solver import ngmres_lsq
+
+    P, _, _, _ = _problem((16, 12, 20), "fp64")
+    rng = np.random.default_rng(16)
+    vecs = [rng.standard_normal(3 * 16 * 12 * 20) for _ in range(64)]
+    out = ga.ga_op_dots(P.ctx, P.dtype, to_dev(vecs[0], "fp64"), [to_dev(x, "fp64") for x in vecs])
+    ref = np.array([float(np.dot(vecs[0], x)) for x in vecs])
+    assert np.max(np.abs(out - ref) / np.abs(ref)) < 1e-12
+    gq, gw = vecs[0], vecs[1:]
+    c = float(gq @ gq)
+    a = np.array([gq @ g for g in gw])
+    M = np.array([[gi @ gj for gj in gw] for gi in gw])
+    beta = ga.ga_op_lsq(P.ctx, c, a, M)
+    assert beta.shape == (63,)
+    np.testing.assert_allclose(beta, ngmres_lsq(gq, gw), rtol=1e-8, atol=1e-11)
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -82,6 +82,27 @@ def test_ga_aa_iterates_match_oracle_fp64(variant, sigma, tau):
     assert abs(st.rho_mem - q.rho_mem) == 0.0
 
 
+def test_mixed_solver_carries_the_regulariser_on_a_512_axis():
+    """H2 on a 512-point axis in mixed precision: the solver carries alpha L v through its linear
+    updates instead of transforming its FP32 iterate, so its iterates and reported gradient norms
+    follow the FP64 oracle's GA-NGMRES run step by step (a transform of v would put an O(1e-2)
+    error into the gradient here, see test_gradient_with_a_512_axis)."""
+    shape = (8, 12, 512)
+    m0, m1, _ = random_problem_fields(shape, 21, vel_scale_vox=1.5)
+    w = dict(m0=m0, m1=m1, nt=4, model="advection", reg_order=2, alpha=1e-3, window=5, sigma=4, tau=2,
+             max_iter=10, rel_tol=0.0)
+    P, O, so = _pair(w, "mixed")
+    hist = []
+    osol.ga_ngmres(O.gradient, osol.ArmijoQ(O), np.zeros((3,) + shape), window=5, sigma=4, tau=2, n_iter=6,
+                   rel_tol=0.0, history=hist)
+    v = to_dev(np.zeros((3,) + shape), "mixed")
+    for k, h in enumerate(hist):
+        st = P.step(v)
+        assert rel_l2(host(v), h["v"]) < 2e-4, (k, rel_l2(host(v), h["v"]))
+        assert abs(st.rel_grad_inf - h["rel_grad"]) <= 2e-3 * h["rel_grad"], (k, st.rel_grad_inf, h["rel_grad"])
+        assert abs(st.obj - h["obj"]) <= 1e-4 * abs(h["obj"])
+
+
 def test_ga_aa_window_zero_is_rpgd():
     """With w = 0 every GA-AA step is a fixed-point step, so the iterates are those of RPGD."""
     w = workload("adv2d64", n=(32, 32))
