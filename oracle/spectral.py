@@ -77,6 +77,16 @@ def grad(f):
     return np.stack([ifftn_real(1j * kt * fh) for kt in deriv_wavenumber_grids(f.shape)])
 
 
+def line_derivative(f_line):
+    """Spectral derivative (grid spacing 2 pi / L) of one periodic grid line of L samples, with the
+    Nyquist entry zeroed. The derivative of a field along axis a restricted to a grid line along a
+    equals this line derivative: the transforms along the other axes cancel."""
+    L = f_line.shape[-1]
+    k = int_wavenumbers(L)
+    kt = np.where(2 * np.abs(k) == L, 0.0, k)
+    return np.real(np.fft.ifft(1j * kt * np.fft.fft(f_line, axis=-1), axis=-1))
+
+
 def div(v):
     """Spectral divergence sum_c F^{-1}[i k~_c F v_c]."""
     kts = deriv_wavenumber_grids(v.shape[1:])

@@ -33,8 +33,8 @@ def grid_index(n):
     return np.stack(np.meshgrid(*[np.arange(ni, dtype=np.float64) for ni in n], indexing="ij"))
 
 
-def departure_points(v, nt, sign):
-    """RK2 departure points in grid units.
+def departure_points_at(v, nt, sign, pts):
+    """RK2 departure points (grid units) of the grid points pts (integer array (d, ...)).
 
     sign=+1 gives X- (state equation, characteristics of v);
     sign=-1 gives X+ (adjoint equation, characteristics of -v).
@@ -42,28 +42,49 @@ def departure_points(v, nt, sign):
     n = v.shape[1:]
     d = v.shape[0]
     ht = 1.0 / nt
-    h = np.array([2.0 * np.pi / ni for ni in n])
-    base = grid_index(n)
-    xstar = np.stack([base[a] - sign * ht * v[a] / h[a] for a in range(d)])
+    h = [2.0 * np.pi / ni for ni in n]
+    pts = np.asarray(pts, dtype=np.int64)
+    vp = np.stack([v[a][tuple(pts)] for a in range(d)])
+    xstar = np.stack([pts[a] - sign * ht * vp[a] / h[a] for a in range(d)])
     vstar = np.stack([interp(v[a], xstar) for a in range(d)])
-    return np.stack([base[a] - sign * 0.5 * ht * (v[a] + vstar[a]) / h[a] for a in range(d)])
+    return np.stack([pts[a] - sign * 0.5 * ht * (vp[a] + vstar[a]) / h[a] for a in range(d)])
+
+
+def departure_points(v, nt, sign):
+    """RK2 departure points in grid units at every grid point (see departure_points_at)."""
+    return departure_points_at(v, nt, sign, grid_index(v.shape[1:]).astype(np.int64))
+
+
+def state_step_at(model, mj, mu, xm, pts, nt):
+    """m_{j+1} at the grid points pts from m_j, given their departure points xm = X-(pts)."""
+    ht = 1.0 / nt
+    p = interp(mj, xm)
+    if model != "continuity":
+        return p
+    s = interp(mj * mu, xm)
+    mup = mu[tuple(np.asarray(pts, dtype=np.int64))]
+    return p - 0.5 * ht * (s + mup * (p - ht * s))
+
+
+def adjoint_step_at(model, ln, mu, xp, pts, nt):
+    """lambda_j at the grid points pts from lambda_{j+1}, given their departure points xp = X+(pts)."""
+    ht = 1.0 / nt
+    big = interp(ln, xp)
+    if model == "continuity":
+        return big
+    s = interp(ln * mu, xp)
+    mup = mu[tuple(np.asarray(pts, dtype=np.int64))]
+    return big + 0.5 * ht * (s + mup * (big + ht * s))
 
 
 def forward_states(model, m0, v, nt, mu=None, xm=None):
     """All states m_0..m_{n_t} of the state equation (advection or continuity)."""
     if xm is None:
         xm = departure_points(v, nt, +1)
-    ht = 1.0 / nt
+    pts = grid_index(np.shape(m0)).astype(np.int64)
     states = [np.array(m0, dtype=np.float64)]
     for _ in range(nt):
-        mj = states[-1]
-        if model == "continuity":
-            p = interp(mj, xm)
-            s = interp(mj * mu, xm)
-            ptilde = p - ht * s
-            states.append(p - 0.5 * ht * (s + mu * ptilde))
-        else:
-            states.append(interp(mj, xm))
+        states.append(state_step_at(model, states[-1], mu, xm, pts, nt))
     return states
 
 
@@ -71,15 +92,9 @@ def adjoint_states(model, lam1, v, nt, mu=None, xp=None):
     """All adjoint states lambda_0..lambda_{n_t} given the terminal value lambda_{n_t} = lam1."""
     if xp is None:
         xp = departure_points(v, nt, -1)
-    ht = 1.0 / nt
+    pts = grid_index(np.shape(lam1)).astype(np.int64)
     lams = [None] * (nt + 1)
     lams[nt] = np.array(lam1, dtype=np.float64)
     for j in range(nt - 1, -1, -1):
-        ln = lams[j + 1]
-        big = interp(ln, xp)
-        if model == "continuity":
-            lams[j] = big
-        else:
-            s = interp(ln * mu, xp)
-            lams[j] = big + 0.5 * ht * (s + mu * (big + ht * s))
+        lams[j] = adjoint_step_at(model, lams[j + 1], mu, xp, pts, nt)
     return lams

@@ -80,3 +80,18 @@ def test_regulariser_energy_closed_form():
         val = 0.5 * sp.inner(v, sp.apply_L(v, s), n)
         exact = 0.5 * 5.0 ** s * (2 * np.pi) ** 2 / 2
         assert abs(val - exact) < 1e-10 * exact
+
+
+def test_line_derivative_closed_form_and_agreement_with_grad():
+    """1D spectral derivative of a grid line: exact for trigonometric polynomials below Nyquist,
+    zero for the Nyquist mode (reading of Sec. 2.2), and equal to the axis component of the 3D
+    spectral gradient on every line of that axis."""
+    L = 24
+    x = 2 * np.pi * np.arange(L) / L
+    np.testing.assert_allclose(sp.line_derivative(np.sin(3 * x) + 0.5 * np.cos(7 * x)),
+                               3 * np.cos(3 * x) - 3.5 * np.sin(7 * x), atol=1e-12)
+    np.testing.assert_allclose(sp.line_derivative(np.cos(L / 2 * x)), 0.0, atol=1e-12)
+    f = np.random.default_rng(4).standard_normal((6, 10, 8))
+    g = sp.grad(f)
+    np.testing.assert_allclose(sp.line_derivative(np.moveaxis(f, 1, -1)), np.moveaxis(g[1], 1, -1), atol=1e-12)
+    np.testing.assert_allclose(sp.line_derivative(np.moveaxis(f, 0, -1)), np.moveaxis(g[0], 0, -1), atol=1e-12)

@@ -121,3 +121,25 @@ def test_adjoint_advection_source_matches_closed_form_for_linear_growth():
     fwd = 1 - 0.5 * ht * (0.7 + 0.7 * (1 - ht * 0.7))
     for j in range(nt + 1):
         np.testing.assert_allclose(pis[j], fwd ** j, rtol=1e-14)
+
+
+def test_point_restricted_steps_equal_the_full_grid():
+    """The per-point departure points and state/adjoint steps (used for sampled parity at full size)
+    give the full-grid values at any set of grid points."""
+    from oracle.transport import adjoint_step_at, departure_points_at, state_step_at
+
+    n = (10, 12, 8)
+    rng = np.random.default_rng(9)
+    v = random_fourier_field(n, 3, 3, rng) * 0.3
+    m = rng.standard_normal(n)
+    mu = sp.div(v)
+    pts = np.stack([rng.integers(0, k, size=40) for k in n])
+    xm_all = departure_points(v, 4, +1)
+    xm = departure_points_at(v, 4, +1, pts)
+    np.testing.assert_allclose(xm, xm_all[(slice(None),) + tuple(pts)], atol=1e-14)
+    for model in ("advection", "continuity"):
+        full = forward_states(model, m, v, 4, mu=mu)[1]
+        np.testing.assert_allclose(state_step_at(model, m, mu, xm, pts, 4), full[tuple(pts)], atol=1e-13)
+        xp = departure_points_at(v, 4, -1, pts)
+        fulla = adjoint_states(model, m, v, 4, mu=mu)[3]
+        np.testing.assert_allclose(adjoint_step_at(model, m, mu, xp, pts, 4), fulla[tuple(pts)], atol=1e-13)
