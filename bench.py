@@ -274,7 +274,8 @@ def run_batch(args):
         d0, d1 = dev(w["m0"]), dev(w["m1"])
         torch.cuda.synchronize()  # pooled streams do not order themselves after the default stream
         P = ga.Problem(d0, d1, nt=w["nt"], model="advection", reg_order=1, alpha=w["alpha"],
-                       prec="mixed", window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2, stream=st.cuda_stream)
+                       prec="mixed", window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2, stream=st.cuda_stream,
+                       graphs=args.graphs)
         ctxs.append(P)
         vs.append(torch.zeros((3,) + tuple(w["n"]), dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
@@ -305,7 +306,8 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch: 32 problems, grids from {64,96,128,160}^3, nt=4, H1, alpha in {1e-2,1e-3}, "
-                                   "GA-NGMRES(5;4,2) to rel-grad 1e-2, one stream per problem"},
+                                   "GA-NGMRES(5;4,2) to rel-grad 1e-2, one stream per problem",
+                       "graphs": bool(args.graphs)},
             "sequential_s_per_batch": seq,
             "per_problem": [{"n": int(w["n"][0]), "alpha": w["alpha"], "iters": st.iters,
                              "grad_evals": st.grad_evals, "converged": bool(st.converged)}
@@ -331,6 +333,8 @@ def main():
                     help="--workload sweep: tolerance of the hyperparameter and alpha parts (mesh: 1e-3)")
     ap.add_argument("--workload", default="cont3d256", choices=["cont3d256", "batch", "sweep"],
                     help="cont3d256 (default) or batch: 32 independent advection problems of uneven size")
+    ap.add_argument("--graphs", action="store_true",
+                    help="--workload batch: replay each problem's repeated evaluations from CUDA graphs")
     ap.add_argument("--compare-methods", action="store_true",
                     help="also time the same solve with GA-AA and RPGD (mixed precision, same settings)")
     ap.add_argument("--fp64-tts", action="store_true",

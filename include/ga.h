@@ -80,6 +80,10 @@ typedef struct {
   int variant;         /* 1: FP step when mod(k, sigma+tau) >= sigma (GA-NGMRES);
                           2: FP step when mod(k, sigma+tau) < tau (aNGMRES(w)[sigma]-FP[tau]) */
   int method;          /* ga_method                                                         */
+  int graphs;          /* 1: capture the evaluations the solver repeats (line-search objective,
+                          gradients) into CUDA graphs on the context stream and replay them; 0: launch
+                          kernel by kernel. Results are the same; graphs cut launch overhead on small
+                          grids and cost 3 vector fields of device memory.                           */
 } ga_solver_opts;
 
 /* Per-context counters and last-iterate metrics (the columns of the paper's tables, Sec. 3.3). */

@@ -33,7 +33,7 @@ class ProblemDesc(ctypes.Structure):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("window", _c_int), ("sigma", _c_int), ("tau", _c_int), ("max_iter", _c_int),
                 ("rel_tol", _c_double), ("armijo_c", _c_double), ("max_backtracks", _c_int),
-                ("variant", _c_int), ("method", _c_int)]
+                ("variant", _c_int), ("method", _c_int), ("graphs", _c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -356,7 +356,7 @@ class Problem:
 
     def __init__(self, m0, m1, nt, model="advection", reg_order=2, alpha=1e-3, prec="fp64",
                  ckpt_every=0, window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2, armijo_c=1e-4,
-                 max_backtracks=20, variant=1, method="ga-ngmres", stream=None):
+                 max_backtracks=20, variant=1, method="ga-ngmres", stream=None, graphs=False):
         shape = tuple(int(s) for s in m0.shape)
         self.shape = shape
         self.dim = len(shape)
@@ -379,6 +379,7 @@ class Problem:
         if method not in methods:
             raise ValueError(f"method must be one of {sorted(methods)}")
         o.method = methods[method]
+        o.graphs = 1 if graphs else 0
         self.desc, self.opts = d, o
         self.ctx = ga_setup(d, o, m0, m1, stream)
 

@@ -15,6 +15,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <unordered_set>
 #include <type_traits>
 
 #include "fft_core.cuh"
@@ -422,7 +423,15 @@ inline int smem_optin_max() {
 template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   if (bytes > (size_t)smem_optin_max()) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
+  // once per kernel: later launches (and launches recorded into a CUDA graph) make no attribute call
+  static std::mutex mu;
+  static std::unordered_set<const void*> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(reinterpret_cast<const void*>(kernel))) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
+  if (e == cudaSuccess) done.insert(reinterpret_cast<const void*>(kernel));
+  return e;
 }
 
 }  // namespace

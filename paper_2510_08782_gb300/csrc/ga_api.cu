@@ -35,7 +35,11 @@ using namespace ga;
 
 namespace ga {
 static std::atomic<long long> g_launches{0};
-void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;  // this thread's share (kernel counts of a capture)
+void note_launches(int n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 }  // namespace ga
 
 namespace {
@@ -123,6 +127,9 @@ template <typename T> struct Engine : EngineBase {
     if (ev[0]) cudaEventDestroy(ev[0]);
     if (ev[1]) cudaEventDestroy(ev[1]);
     for (auto e : prof_ev) cudaEventDestroy(e);
+    for (auto ge : gexec)
+      if (ge) cudaGraphExecDestroy(ge);
+    if (gst) cudaStreamDestroy(gst);
   }
 
   void ck(cudaError_t e, const char* what) {
@@ -224,6 +231,13 @@ template <typename T> struct Engine : EngineBase {
     }
     S = dalloc<T>(2 * vl);
     wtmp = dalloc<T>(vl);
+    graphs = c->opts.graphs != 0;
+    if (graphs) {
+      gin = dalloc<T>(2 * vl);
+      gbuf = dalloc<T>(vl);
+      if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+        ck(cudaStreamCreate(&gst), "capture stream");
+    }
     dM = dalloc<double>((long long)W1 * W1);
     dbeta = dalloc<double>(kMaxWin + 4);
     ck(cudaMemsetAsync(dM, 0, sizeof(double) * W1 * W1, st), "memset");
@@ -366,23 +380,70 @@ template <typename T> struct Engine : EngineBase {
     return seg + (long long)(j - js - 1) * nv;
   }
 
-  void read_results(int count) {
+  void issue_results(int count) {
     ck(cudaMemcpyAsync(hres, dres, sizeof(double) * count, cudaMemcpyDeviceToHost, st), "result copy");
+  }
+  void wait_results() {
     ck(cudaStreamSynchronize(st), "sync");
     prof_flush();
+  }
+  void read_results(int count) {
+    issue_results(count);
+    wait_results();
+  }
+
+  // ---- CUDA graphs of the solver's evaluations (ga_solver_opts.graphs) ---------------------------
+  // The evaluations the solver repeats run on fixed buffers: v and w are copied into gin, the gradient
+  // comes out of gbuf and s goes to S. Variant id's first call runs eagerly (it loads every kernel and
+  // sets every launch attribute), the second is captured into a graph, later calls replay it.
+  enum { G_OBJ = 0, G_OBJ_KEEP = 1, G_GRAD = 2, G_GRAD_REUSE = 3, G_GRAD_S = 4, G_GRAD_REUSE_S = 5, G_NUM = 6 };
+  bool graphs = false;
+  // A default stream cannot be captured: graphs are then captured and replayed on a private blocking
+  // stream, which orders itself against the legacy default stream in both directions.
+  cudaStream_t gst = nullptr;
+  T* gin = nullptr;
+  T* gbuf = nullptr;
+  cudaGraphExec_t gexec[G_NUM] = {};
+  long long gkernels[G_NUM] = {};
+  int gcalls[G_NUM] = {};
+
+  template <typename F> void run_variant(int id, F&& enqueue) {
+    if (gcalls[id]++ == 0) {
+      enqueue();
+      return;
+    }
+    cudaStream_t cs = gst ? gst : st;
+    if (!gexec[id]) {
+      const long long c0 = t_launches;
+      ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+      cudaStream_t saved = st;
+      st = cs;  // every launch of enqueue() goes to the captured stream
+      cudaGraph_t graph = nullptr;
+      try {
+        enqueue();
+      } catch (...) {
+        st = saved;
+        cudaStreamEndCapture(cs, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      st = saved;
+      ck(cudaStreamEndCapture(cs, &graph), "end capture");
+      const cudaError_t e = cudaGraphInstantiate(&gexec[id], graph, 0);
+      cudaGraphDestroy(graph);
+      ck(e, "graph instantiate");
+      gkernels[id] = t_launches - c0;
+      note_launches((int)-gkernels[id]);  // recorded, not launched
+    }
+    ck(cudaGraphLaunch(gexec[id], cs), "graph launch");
+    note_launches((int)gkernels[id]);
   }
 
   // obj(v): one state solve. Results: dres[0] = sum (m(1) - m1)^2, dres[1] = regulariser sum.
   // With keep = true the state solve stores its trajectory (and v^, mu, X-) so that an immediately
   // following gradient(v) on the same, unmodified buffer reuses them instead of solving again.
   // w = alpha L v when the caller carries it (the solver), else nullptr (computed by the transform).
-  double objective(const T* v, double* mismatch = nullptr, bool keep = false, const T* w = nullptr) {
-    fwd_cache = nullptr;
-    ck(cudaEventRecord(ev[0], st), "event");
-    if (!w) {
-      apply_alphaL(v, wtmp);
-      w = wtmp;
-    }
+  void enqueue_objective(const T* v, const T* w, bool keep) {
     reg_dot(v, w, 1);
     if (needs_mu_forward() || keep) compute_mu(v);
     const T* mT;
@@ -394,8 +455,24 @@ template <typename T> struct Engine : EngineBase {
       mT = forward_final(v);
     }
     ck(launch_mismatch<T>(mT, m1, nullptr, nv, dpart, dres, st), "mismatch");
+    issue_results(2);
+  }
+  double objective(const T* v, double* mismatch = nullptr, bool keep = false, const T* w = nullptr) {
+    fwd_cache = nullptr;
+    ck(cudaEventRecord(ev[0], st), "event");
+    if (graphs && w && prof_class < 0) {
+      ck(cudaMemcpyAsync(gin, v, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy v");
+      ck(cudaMemcpyAsync(gin + vl, w, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy w");
+      run_variant(keep ? G_OBJ_KEEP : G_OBJ, [&] { enqueue_objective(gin, gin + vl, keep); });
+    } else {
+      if (!w) {
+        apply_alphaL(v, wtmp);
+        w = wtmp;
+      }
+      enqueue_objective(v, w, keep);
+    }
     ck(cudaEventRecord(ev[1], st), "event");
-    read_results(2);
+    wait_results();
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
     ctx->stats.t_obj_ms += ms;
@@ -411,6 +488,7 @@ template <typename T> struct Engine : EngineBase {
   // Body force b (not projected) from the adjoint started at lam_init (lam_init may be lam[0]).
   // Requires departure points, mu and the forward states.
   void body_force(const T* lam_init) {
+    seg_base = -1;  // recompute every segment: the sequence of launches is the same on every call
     ck(cudaMemsetAsync(body, 0, sizeof(T) * vl, st), "memset body");
     const T* lcur = lam_init;
     int pp = (lam_init == lam[0]) ? 1 : 0;
@@ -436,14 +514,7 @@ template <typename T> struct Engine : EngineBase {
   // solver through every linear update of v, so the regulariser term never passes through a transform
   // of v whose rounding the symbol |k|^{2s} would amplify; nullptr computes it by the transform. When
   // s_out != nullptr, writes s = -(alpha L)^{-1} (P) g to s_out and alpha L s to s_out + vl.
-  double gradient(const T* v, T* gout, T* s_out, double* mismatch = nullptr, const T* w = nullptr) {
-    ck(cudaEventRecord(ev[0], st), "event");
-    const bool reuse = fwd_cache == v;  // trajectory of the last objective(v, .., keep) call
-    fwd_cache = nullptr;
-    if (!w) {
-      apply_alphaL(v, wtmp);
-      w = wtmp;
-    }
+  void enqueue_gradient(const T* v, const T* w, T* gout, T* s_out, bool reuse) {
     reg_dot(v, w, 1);
     if (reuse) {
       // mu, X- and the stored states are those of v: only X+ is missing
@@ -464,8 +535,27 @@ template <typename T> struct Engine : EngineBase {
     ck(launch_axpy<T>(gout, body, w, 1.0, vl, st), "g = (P) b + w");
     if (s_out) precond_into(gout, s_out, s_out + vl);
     ck(launch_maxabs<T>(gout, vl, dpart, dres + 2, st), "maxabs");
+    issue_results(3);
+  }
+  double gradient(const T* v, T* gout, T* s_out, double* mismatch = nullptr, const T* w = nullptr) {
+    ck(cudaEventRecord(ev[0], st), "event");
+    const bool reuse = fwd_cache == v;  // trajectory of the last objective(v, .., keep) call
+    fwd_cache = nullptr;
+    if (graphs && w && prof_class < 0 && (!s_out || s_out == S)) {
+      ck(cudaMemcpyAsync(gin, v, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy v");
+      ck(cudaMemcpyAsync(gin + vl, w, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy w");
+      const int id = s_out ? (reuse ? G_GRAD_REUSE_S : G_GRAD_S) : (reuse ? G_GRAD_REUSE : G_GRAD);
+      run_variant(id, [&] { enqueue_gradient(gin, gin + vl, gbuf, s_out, reuse); });
+      ck(cudaMemcpyAsync(gout, gbuf, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy g");
+    } else {
+      if (!w) {
+        apply_alphaL(v, wtmp);
+        w = wtmp;
+      }
+      enqueue_gradient(v, w, gout, s_out, reuse);
+    }
     ck(cudaEventRecord(ev[1], st), "event");
-    read_results(3);
+    wait_results();
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
     ctx->stats.t_grad_ms += ms;
@@ -859,7 +949,7 @@ ga_status ga_setup(const ga_problem_desc* desc, const ga_solver_opts* opts, cons
   ok = ok && o.window >= 0 && o.window < kMaxWin && o.window + 2 <= kMaxDots && o.sigma >= 1 && o.tau >= 0 &&
        o.max_iter >= 1 && o.rel_tol >= 0.0 && o.armijo_c > 0.0 && o.max_backtracks >= 0 &&
        o.max_backtracks <= 200 && (o.variant == 1 || o.variant == 2) &&
-       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD || o.method == GA_METHOD_GA_AA);
+       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD || o.method == GA_METHOD_GA_AA) && (o.graphs == 0 || o.graphs == 1);
   if (!ok) {
     g_setup_err = "invalid problem descriptor or solver options";
     return GA_ERR_ARG;

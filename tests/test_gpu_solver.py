@@ -170,9 +170,32 @@ def test_exhausted_line_search_is_reported():
     assert "Armijo" in str(e.value)
 
 
-def test_batch_of_uneven_problems_matches_individual_solves():
-    """The batched form: uneven problems, each on its own stream, solved concurrently, give the
-    same iterates as one-at-a-time solves."""
+@pytest.mark.parametrize("model,method,shape,prec", [("advection", "ga-ngmres", (20, 16, 24), "mixed"),
+                                                      ("continuity", "ga-ngmres", (16, 12, 20), "mixed"),
+                                                      ("incompressible", "ga-ngmres", (16, 16, 16), "mixed"),
+                                                      ("advection", "ga-aa", (32, 24), "fp64")])
+def test_graph_replay_equals_kernel_by_kernel(model, method, shape, prec):
+    """Capturing the solver's evaluations into CUDA graphs changes nothing: iterates and statistics of
+    9 iterations are bitwise equal to kernel-by-kernel launches (every variant is first run eagerly,
+    then captured, then replayed)."""
+    m0, m1, _ = random_problem_fields(shape, 33, model=model, vel_scale_vox=1.2)
+    w = dict(m0=m0, m1=m1, nt=4, model=model, reg_order=1, alpha=1e-2, window=4, sigma=2, tau=1, max_iter=20,
+             rel_tol=0.0)
+    P0, _, _ = _pair(w, prec, method=method)
+    P1, _, _ = _pair(w, prec, method=method, graphs=True)
+    v0 = to_dev(np.zeros((len(shape),) + shape), prec)
+    v1 = to_dev(np.zeros((len(shape),) + shape), prec)
+    for _ in range(9):
+        s0, s1 = P0.step(v0), P1.step(v1)
+        assert np.array_equal(host(v0), host(v1))
+        assert (s0.obj, s0.rel_grad_inf, s0.last_branch, s0.ls_trials) == (s1.obj, s1.rel_grad_inf, s1.last_branch,
+                                                                           s1.ls_trials)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_batch_of_uneven_problems_matches_individual_solves(graphs):
+    """The batched form: uneven problems, each on its own stream (and, with graphs, replaying its
+    captured evaluations), solved concurrently, give the same iterates as one-at-a-time solves."""
     import torch
 
     from paper_2510_08782_gb300 import ga_solve_batch
@@ -182,7 +205,7 @@ def test_batch_of_uneven_problems_matches_individual_solves():
         m0, m1, _ = random_problem_fields(n, 40 + i, vel_scale_vox=1.0)
         w = dict(m0=m0, m1=m1, nt=4, model="advection", reg_order=1, alpha=1e-2, window=5, sigma=4,
                  tau=2, max_iter=15, rel_tol=1e-2)
-        P, _, _ = _pair(w, "mixed", stream=torch.cuda.Stream().cuda_stream)
+        P, _, _ = _pair(w, "mixed", stream=torch.cuda.Stream().cuda_stream, graphs=graphs)
         Q, _, _ = _pair(w, "mixed")
         probs.append(P)
         vs.append(to_dev(np.zeros((3,) + n), "mixed"))
