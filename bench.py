@@ -67,6 +67,21 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_over_ranks(ms, units, device="cuda"):
+    """Whole-job figures of one timed region: the slowest rank's time and the units all ranks
+    processed (a no-op without an initialised process group of more than one rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -266,7 +281,15 @@ def run_batch(args):
     build.build()
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    probs = batch_workloads(32, seed=0)
+    if ws > 1:  # weak scaling: every rank solves its own batch of 32 (seeded by the rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    probs = batch_workloads(32, seed=rank)
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
     streams = [torch.cuda.Stream() for _ in probs]
     ctxs, vs = [], []
@@ -288,11 +311,12 @@ def run_batch(args):
 
     for _ in range(args.warmup):
         solve_all()
+    barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         stats, status = solve_all()
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    barrier()
+    dt, solved = aggregate_over_ranks(time.perf_counter() - t0, len(probs) * args.steps)
     # the same problems solved one after another, for comparison
     t1 = time.perf_counter()
     for P, v in zip(ctxs, vs):
@@ -301,8 +325,12 @@ def run_batch(args):
         P.solve(v)
     torch.cuda.synchronize()
     seq = time.perf_counter() - t1
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
     line = {"metric": "problems solved to rel-grad 1e-2 per second (batch of 32 uneven 3D advection problems)",
-            "value": len(probs) * args.steps / dt, "unit": "problems/s", "n_gpus": 1, "steps": args.steps,
+            "value": solved / dt, "unit": "problems/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch: 32 problems, grids from {64,96,128,160}^3, nt=4, H1, alpha in {1e-2,1e-3}, "
@@ -404,15 +432,7 @@ def main():
     launches = ga.ga_kernel_launches() - launches0
     ms = e0.elapsed_time(e1)
     grad_evals = st.grad_evals
-    if ws > 1:
-        t = torch.tensor([ms, float(grad_evals)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        ms_max, total_evals = float(tmax[0]), float(tsum[1])
-    else:
-        ms_max, total_evals = ms, float(grad_evals)
+    ms_max, total_evals = aggregate_over_ranks(ms, grad_evals)
     value = total_evals / (ms_max / 1e3)
     step_stats = st.as_dict()
 
@@ -569,12 +589,8 @@ def main():
             sq = Q.step(hv)
         Q.close()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t[0])
-        e2e = {"value": ws * sq.grad_evals / dt, "unit": UNIT,
+        dt, e2e_evals = aggregate_over_ranks(time.perf_counter() - t0, sq.grad_evals)
+        e2e = {"value": e2e_evals / dt, "unit": UNIT,
                "h2d_bytes_per_step": int((2 * nv + 3 * nv) * 4 / args.steps),
                "d2h_bytes_per_step": int(3 * nv * 4),
                "note": "timed: ga_setup from pinned host m0/m1 + K ga_step calls with a pinned host v "
