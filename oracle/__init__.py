@@ -15,6 +15,8 @@ Modules
              AA(w) (Alg. 2), GA-NGMRES(w; sigma, tau) (Alg. 3), dense GMRES for the linear-case pins
   diagnostics  deformation map y = x + h u and det grad y (continuity solve from 1), with a spectral
              det(I + grad(h u)) cross-check route
+  dto        discretise-then-optimise gradient of the advection objective: transpose scatter adjoint,
+             derivative of the interpolant, chain rule through the RK2 departure points
 
 Readings of passages the paper leaves silent, garbled or ambiguous are stated in each
 function's docstring. Parity status: every function is pinned by a CPU test against a
