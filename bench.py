@@ -363,6 +363,8 @@ def main():
                     help="cont3d256 (default) or batch: 32 independent advection problems of uneven size")
     ap.add_argument("--graphs", action="store_true",
                     help="--workload batch: replay each problem's repeated evaluations from CUDA graphs")
+    ap.add_argument("--dto", action="store_true",
+                    help="also time the discretise-then-optimise gradient (advection transport, same data)")
     ap.add_argument("--compare-methods", action="store_true",
                     help="also time the same solve with GA-AA and RPGD (mixed precision, same settings)")
     ap.add_argument("--fp64-tts", action="store_true",
@@ -573,6 +575,32 @@ def main():
     torch.cuda.synchronize()
     grad_only = reps / (e0.elapsed_time(e1) / 1e3)
 
+    # ---- discretise-then-optimise gradient (optional): advection transport of the same data ----
+    dto_res = None
+    if args.dto:
+        sa = dict(SETTINGS, model="advection")
+        Pa = ga.Problem(m0, m1, prec="mixed", **sa)
+        va = torch.from_numpy(np.ascontiguousarray(0.5 * w["v_true"], dtype=np.float32)).cuda()
+        go, gd = torch.empty_like(v), torch.empty_like(v)
+        Pa.gradient(va, go)
+        Pa.gradient_dto(va, gd)
+        torch.cuda.synchronize()
+        rates = {}
+        for name, fn, out in (("otd", Pa.gradient, go), ("dto", Pa.gradient_dto, gd)):
+            e0.record()
+            for _ in range(3):
+                fn(va, out)
+            e1.record()
+            torch.cuda.synchronize()
+            rates[name] = 3 / (e0.elapsed_time(e1) / 1e3)
+        rel = float(torch.linalg.vector_norm((gd - go).double()) / torch.linalg.vector_norm(go.double()))
+        dto_res = {"model": "advection transport of the same data and settings, v = v_true / 2",
+                   "dto_grad_evals_per_s": rates["dto"], "otd_grad_evals_per_s": rates["otd"],
+                   "rel_l2_dto_vs_otd": rel}
+        Pa.close()
+        del Pa, va, go, gd
+        torch.cuda.empty_cache()
+
     # ---- end to end through host buffers: setup from host m0/m1, K steps with a host v ----
     e2e = None
     if not args.no_e2e:
@@ -610,7 +638,7 @@ def main():
                            "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "methods_tts": methods, "deformation": deformation, "grad_only_evals_per_s": grad_only,
+                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "methods_tts": methods, "deformation": deformation, "dto": dto_res, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in
                                                                        ("iters", "obj_evals", "rel_grad_inf", "obj",
                                                                         "rho_mem")}}

@@ -132,6 +132,15 @@ ga_status ga_gradient(ga_ctx* ctx, const void* v, void* g, int mem, double* obj)
  * of the transported uniform measure). Uses the context's n_t and grid; 2 + dim state solves. */
 ga_status ga_deformation(ga_ctx* ctx, const void* v, void* u, void* detj, int mem);
 
+/* Gradient of the discrete objective (discretise-then-optimise; the solver and ga_gradient use the
+ * paper's optimise-then-discretise gradient, Sec. 2.1): with m_{j+1} = A m_j the semi-Lagrangian step,
+ * g = alpha L v + (1/h^d) dJ_data/dv, the data part from the transposed (scattered) interpolation, the
+ * derivative of the cubic interpolant at the departure points and the chain rule through the RK2
+ * departure points (incompressible model: P applied to it). Advection and incompressible models only
+ * (GA_ERR_ARG for the continuity model). Agrees with finite differences of obj(v) to their truncation
+ * error. FP32 results vary at the rounding level between runs (atomic scatter order). */
+ga_status ga_gradient_dto(ga_ctx* ctx, const void* v, void* g, int mem, double* obj);
+
 /* Preconditioned direction s = -(alpha L)^{-1} g with zero symbol entries of L set to one
  * (Sec. 2.2, Eq. (9)); incompressible model: s = -(alpha L)^{-1} P g. */
 ga_status ga_precond(ga_ctx* ctx, const void* g, void* s, int mem);

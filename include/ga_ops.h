@@ -78,6 +78,12 @@ ga_status ga_transport(ga_ctx* ctx, const void* v, void* m1_out, int mem);
  * ga_op_body_force. Elementwise (l2) gradients in and out. */
 ga_status ga_transport_vjp(ga_ctx* ctx, const void* v, const void* gamma, void* grad_v, int mem);
 
+/* Exact vector-Jacobian product of ga_transport (discretise-then-optimise): the gradient with respect
+ * to the grid values of v of <gamma, m(1)(v)> for the discrete semi-Lagrangian transport (advection;
+ * the incompressible model transports by advection too). GA_ERR_ARG for the continuity model.
+ * Elementwise (l2) gradients in and out. */
+ga_status ga_transport_vjp_exact(ga_ctx* ctx, const void* v, const void* gamma, void* grad_v, int mem);
+
 /* Device-time accounting of one kernel class over a region of calls, with CUDA events recorded
  * on the context stream around every launch of that class: 0 = semi-Lagrangian state steps,
  * 1 = fused FFT-derivative passes, 2 = 3D FFT transforms (all passes of one transform),

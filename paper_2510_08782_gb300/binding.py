@@ -89,6 +89,8 @@ _SIGS = {
                    ctypes.POINTER(_c_double)], _c_int),
     "ga_transport": ([_vp, _vp, _vp, _c_int], _c_int),
     "ga_transport_vjp": ([_vp, _vp, _vp, _vp, _c_int], _c_int),
+    "ga_transport_vjp_exact": ([_vp, _vp, _vp, _vp, _c_int], _c_int),
+    "ga_gradient_dto": ([_vp, _vp, _vp, _c_int, ctypes.POINTER(_c_double)], _c_int),
     "ga_prof_start": ([_vp, _c_int], _c_int),
     "ga_prof_stop": ([_vp, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)], _c_int),
     "ga_kernel_launches": ([], ctypes.c_longlong),
@@ -246,6 +248,18 @@ def ga_transport(ctx, dtype, v, m1_out):
 def ga_transport_vjp(ctx, dtype, v, gamma, grad_v):
     (pv, pgam, pg), mem = _ptrs(dtype, v, gamma, grad_v)
     _check(lib().ga_transport_vjp(ctx, pv, pgam, pg, mem), ctx)
+
+
+def ga_transport_vjp_exact(ctx, dtype, v, gamma, grad_v):
+    (pv, pgam, pg), mem = _ptrs(dtype, v, gamma, grad_v)
+    _check(lib().ga_transport_vjp_exact(ctx, pv, pgam, pg, mem), ctx)
+
+
+def ga_gradient_dto(ctx, dtype, v, g):
+    (pv, pg), mem = _ptrs(dtype, v, g)
+    out = _c_double()
+    _check(lib().ga_gradient_dto(ctx, pv, pg, mem, ctypes.byref(out)), ctx)
+    return out.value
 
 
 def _dev(dtype, *arrays):
@@ -423,5 +437,9 @@ class Problem:
     def transport(self, v, m1_out):
         ga_transport(self.ctx, self.dtype, v, m1_out)
 
-    def transport_vjp(self, v, gamma, grad_v):
-        ga_transport_vjp(self.ctx, self.dtype, v, gamma, grad_v)
+    def transport_vjp(self, v, gamma, grad_v, exact=False):
+        (ga_transport_vjp_exact if exact else ga_transport_vjp)(self.ctx, self.dtype, v, gamma, grad_v)
+
+    def gradient_dto(self, v, g):
+        """Gradient of the discrete objective (discretise-then-optimise); returns obj(v)."""
+        return ga_gradient_dto(self.ctx, self.dtype, v, g)

@@ -609,6 +609,76 @@ template <typename T> struct Engine : EngineBase {
     if (a != detj) ck(cudaMemcpyAsync(detj, a, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st), "copy det");
   }
 
+  // ---- discretise-then-optimise gradient (advection transport; dto_kernels.cu) --------------------
+  T* dto_buf = nullptr;  // Euclidean velocity gradient of the data term (allocated on first use)
+
+  void dto_require_advection(const char* what) {
+    if (model == GA_MODEL_CONTINUITY) {
+      set_err(ctx, "%s: the discrete gradient is built for the advection transport (advection and "
+                   "incompressible models)", what);
+      throw Fail{GA_ERR_ARG};
+    }
+  }
+  // Departure points and the forward states of v (stored or checkpointed).
+  void dto_forward(const T* v) {
+    ck(launch_departure<T>(g, v, xm, xp, (T)ht, st, /*both=*/0), "departure");
+    forward_all();
+  }
+  // Euclidean gradient of coef <rT, m_{n_t}(v)> with respect to the grid values of v, into out:
+  // r_{n_t} = rT, r_j = A^T r_{j+1}, G += coef r_{j+1} grad I[m_j](X-), then the chain rule through X-.
+  void dto_backward(const T* v, const T* rT, double coef, T* out) {
+    T* G = body;
+    ck(cudaMemsetAsync(G, 0, sizeof(T) * vl, st), "memset G");
+    if (rT != lam[0]) ck(cudaMemcpyAsync(lam[0], rT, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st), "copy r");
+    int pp = 0;
+    seg_base = -1;
+    for (int j = nt - 1; j >= 0; --j) {
+      const T* mj = state(j);
+      ck(launch_dto_accum<T>(g, lam[pp], mj, xm, G, (T)coef, st), "dto accumulate");
+      if (j > 0) {
+        ck(cudaMemsetAsync(lam[pp ^ 1], 0, sizeof(T) * nv, st), "memset r");
+        ck(launch_interp_scatter<T>(g, lam[pp], xm, lam[pp ^ 1], st), "interpolation transpose");
+        pp ^= 1;
+      }
+    }
+    ck(launch_dto_velocity<T>(g, v, G, out, (T)ht, st), "dto velocity");
+  }
+  // L2 gradient of the discrete objective: alpha L v + (P) (1/h^d) dJ_data/dv.
+  double gradient_dto(const T* v, T* gout, double* mismatch) {
+    dto_require_advection("ga_gradient_dto");
+    if (!dto_buf) dto_buf = dalloc<T>(vl);
+    fwd_cache = nullptr;
+    ck(cudaEventRecord(ev[0], st), "event");
+    apply_alphaL(v, wtmp);
+    reg_dot(v, wtmp, 1);
+    dto_forward(v);
+    ck(launch_mismatch<T>(slot(nt), m1, lam[0], nv, dpart, dres, st), "mismatch");  // lam[0] = m1 - m(1)
+    dto_backward(v, lam[0], -hd, dto_buf);  // r = h^d (m(1) - m1) = -h^d lam[0]
+    if (model == GA_MODEL_INCOMPRESSIBLE) {
+      for (int c = 0; c < dim; ++c) r2c(dto_buf + c * nv, bh + c * g.nhalf);
+      SpecArgs sp{SPEC_LERAY, s, alpha, 1, 0};
+      ck(launch_spectral<T>(g, sp, bh, nullptr, st), "spectral leray");
+      for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, dto_buf + c * nv);
+    }
+    ck(launch_axpy<T>(gout, wtmp, dto_buf, 1.0 / hd, vl, st), "g = alpha L v + b / h^d");
+    ck(launch_maxabs<T>(gout, vl, dpart, dres + 2, st), "maxabs");
+    ck(cudaEventRecord(ev[1], st), "event");
+    read_results(3);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ctx->stats.t_grad_ms += ms;
+    ctx->stats.grad_evals += 1;
+    ctx->stats.pde_solves += 2;
+    const double m = 0.5 * hd * hres[0];
+    if (mismatch) *mismatch = m;
+    const double val = m + reg_value(hres[1]);
+    if (!std::isfinite(val) || !std::isfinite(hres[2])) {
+      set_err(ctx, "non-finite objective or gradient (obj=%g, |g|inf=%g)", val, hres[2]);
+      throw Fail{GA_ERR_NAN};
+    }
+    return val;
+  }
+
   // ---- solver (Alg. 3) -----------------------------------------------------------------------------
   void reset() {
     while (!win.empty()) {
@@ -1028,6 +1098,18 @@ ga_status ga_deformation(ga_ctx* ctx, const void* v, void* u, void* detj, int me
   });
 }
 
+ga_status ga_gradient_dto(ga_ctx* ctx, const void* v, void* g, int mem, double* obj) {
+  if (!ctx || !v || !g || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    auto* vin = stage_in(e, v, e.vl, mem, e.io_a);
+    T* gout = mem == GA_MEM_DEVICE ? static_cast<T*>(g) : e.io_b;
+    const double J = e.gradient_dto(vin, gout, nullptr);
+    if (obj) *obj = J;
+    stage_out(e, g, gout, e.vl, mem);
+  });
+}
+
 ga_status ga_precond(ga_ctx* ctx, const void* g, void* s, int mem) {
   if (!ctx || !g || !s || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
   return dispatch(ctx, [&](auto& e) {
@@ -1294,6 +1376,19 @@ ga_status ga_transport_vjp(ga_ctx* ctx, const void* v, const void* gamma, void* 
     e.body_force(e.lam[0]);
     // grad_v = -b
     e.ck(launch_axpy<T>(e.io_b, e.body, e.body, -2.0, e.vl, e.st), "negate");
+    stage_out(e, grad_v, e.io_b, e.vl, mem);
+  });
+}
+
+ga_status ga_transport_vjp_exact(ga_ctx* ctx, const void* v, const void* gamma, void* grad_v, int mem) {
+  if (!ctx || !v || !gamma || !grad_v || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
+  return dispatch(ctx, [&](auto& e) {
+    using T = typename std::remove_reference<decltype(*e.m0)>::type;
+    e.dto_require_advection("ga_transport_vjp_exact");
+    auto* vin = stage_in(e, v, e.vl, mem, e.io_a);
+    const T* gam = stage_in(e, gamma, e.nv, mem, e.lam[0]);
+    e.dto_forward(vin);
+    e.dto_backward(vin, gam, 1.0, e.io_b);
     stage_out(e, grad_v, e.io_b, e.vl, mem);
   });
 }

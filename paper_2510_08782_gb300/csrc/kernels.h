@@ -89,6 +89,13 @@ cudaError_t launch_mismatch(const T* mT, const T* m1, T* lam, long long len, dou
                             double* out, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* partial, int count, int nblocks, double* out, cudaStream_t st);
 // y = x + a s
+// discretise-then-optimise sweep (dto_kernels.cu)
+template <typename T>
+cudaError_t launch_dto_accum(const Grid& g, const T* r, const T* m, const T* disp, T* G, T coef, cudaStream_t st);
+template <typename T>
+cudaError_t launch_interp_scatter(const Grid& g, const T* r, const T* disp, T* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dto_velocity(const Grid& g, const T* v, const T* G, T* out, T ht, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fill(T* y, double value, long long len, cudaStream_t st);
 template <typename T>

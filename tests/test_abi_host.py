@@ -93,6 +93,8 @@ def test_null_arguments_rejected(libga):
     assert L.ga_gradient(None, None, None, 0, None) == 1
     assert L.ga_step(None, None, 0, None) == 1
     assert L.ga_deformation(None, None, None, None, 0) == 1
+    assert L.ga_gradient_dto(None, None, None, 0, None) == 1
+    assert L.ga_transport_vjp_exact(None, None, None, None, 0) == 1
     assert L.ga_solve_batch(-1, None, None, 0, None) == 1
     assert L.ga_setup(None, None, None, None, 0, None, None) == 1
 
