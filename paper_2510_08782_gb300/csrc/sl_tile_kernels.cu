@@ -19,6 +19,7 @@ namespace ga {
 namespace {
 
 constexpr int BX = 32, BY = 8, BZ = 8, H = 2;
+constexpr int kTileThreads = 32 * BY;  // one warp per brick row
 constexpr int TY = BY + 2 * H + 2, TZ = BZ + 2 * H + 2;  // 14, 14 (x extent: TXA below)
 
 __device__ __forceinline__ int wrap_any(int a, int n) {
@@ -99,6 +100,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // Staged tile: x extent TXA = 40 starting at bx*BX - 4 (16-byte aligned), y and z as before.
 constexpr int TXA = 40, XOFF = 4;
 constexpr int TILEA = TXA * TY * TZ;
+// Two-field steps interleave (f, f mu) into 8-byte pairs with their own row pitch TXP (>= TXA). Padded
+// pitches (41, 44) spread rows and planes of the 64-bit accesses over more banks but measured slower
+// than TXP = TXA on GB300, so the pairs keep the staging layout.
+constexpr int TXP = 40;
+constexpr int TILEP = TXP * TY * TZ;
 
 struct BrickIdx {
   int bx, by, bz;
@@ -164,8 +170,9 @@ template <typename V> __device__ __forceinline__ void lagrange4v(V t, V* w) {
 }
 
 // Tensor-product sum of the 4 x 4 x 4 taps returned by ld(offset) (offset relative to the stencil's
-// first tap, in tile elements): 16 rows along x, then 4 columns along y, then z.
-template <typename V, typename Load>
+// first tap, in tile elements; PITCH elements per tile row): 16 rows along x, then 4 columns along y,
+// then z.
+template <int PITCH, typename V, typename Load>
 __device__ __forceinline__ V interp64(const V* wz, const V* wy, const V* wx, Load ld) {
   V acc;
 #pragma unroll
@@ -173,7 +180,7 @@ __device__ __forceinline__ V interp64(const V* wz, const V* wy, const V* wx, Loa
     V ay;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int o = (c * TY + b) * TXA;
+      const int o = (c * TY + b) * PITCH;
       V r = vmul(ld(o), wx[0]);
       r = vfma(ld(o + 1), wx[1], r);
       r = vfma(ld(o + 2), wx[2], r);
@@ -190,10 +197,10 @@ __device__ __forceinline__ bool in_halo(float fz, float fy, float fx) {
 }
 
 // One voxel (brick-local z index v, global index idx): shared-memory taps when the stencil lies in the
-// halo, global taps otherwise.
+// halo, global taps otherwise. Two-field steps read the interleaved (f, f mu) tile `sf`.
 template <int MODE>
 __device__ __forceinline__ void sl_single(const float* __restrict__ f, const float* __restrict__ mu,
-                                          float* __restrict__ out, const float* sf, const float* sg, int col,
+                                          float* __restrict__ out, const float* sf, int col,
                                           long long idx, int gz, int v, int gy, int gx, float vz, float vy, float vx,
                                           int n0, int n1, int n2, float ht) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
@@ -204,9 +211,14 @@ __device__ __forceinline__ void sl_single(const float* __restrict__ f, const flo
     lagrange4v(vz - fz, wz);
     lagrange4v(vy - fy, wy);
     lagrange4v(vx - fx, wx);
-    const int base = col + ((v + H + (int)fz) * TY + (int)fy) * TXA + (int)fx;
-    P = interp64<float>(wz, wy, wx, [&](int o) { return sf[base + o]; });
-    if (NF == 2) S = interp64<float>(wz, wy, wx, [&](int o) { return sg[base + o]; });
+    if (NF == 2) {  // col is the pair-layout index here
+      const int base = col + ((v + H + (int)fz) * TY + (int)fy) * TXP + (int)fx;
+      P = interp64<TXP, float>(wz, wy, wx, [&](int o) { return sf[2 * (base + o)]; });
+      S = interp64<TXP, float>(wz, wy, wx, [&](int o) { return sf[2 * (base + o) + 1]; });
+    } else {
+      const int base = col + ((v + H + (int)fz) * TY + (int)fy) * TXA + (int)fx;
+      P = interp64<TXA, float>(wz, wy, wx, [&](int o) { return sf[base + o]; });
+    }
   } else {
     gather_global<NF>(f, mu, gz, gy, gx, vz, vy, vx, n0, n1, n2, P, S);
   }
@@ -230,7 +242,7 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;  // staged fields: f (and f * mu)
   extern __shared__ __align__(16) float smem[];
   const float* sf = smem;
-  const float* sg = smem + TILEA;
+  const float2* sp = reinterpret_cast<const float2*>(smem);  // two-field steps: (f, f mu) per element
   const long long nv = (long long)n0 * n1 * n2;
   const long long plane = (long long)n1 * n2;
   const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
@@ -254,15 +266,36 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
     xa = disp[2 * nv + ia], xb = disp[2 * nv + ib];
     if (NF == 2) ma = mu[ia], mb = mu[ib];
   };
-  if (active && nz >= 2) fetch(0);
+  if (NF == 1 && active && nz >= 2) fetch(0);
   asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
-  if (NF == 2) {  // each element is read and written by one thread only
-    for (int e = threadIdx.x; e < TILEA; e += blockDim.x) smem[TILEA + e] *= smem[e];
+  if (NF == 2) {
+    // Interleave in place: the f and mu tiles (TILEA floats each) become TILEA pairs (f, f mu) over the
+    // same bytes, so a tap of both fields is one 64-bit shared load. Every thread holds its elements
+    // in registers across the barrier, since a pair overwrites other threads' source elements.
+    constexpr int PER = (TILEA + kTileThreads - 1) / kTileThreads;
+    float fa[PER], fm[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + kTileThreads * i;
+      if (e < TILEA) {
+        fa[i] = smem[e];
+        fm[i] = fa[i] * smem[TILEA + e];
+      }
+    }
+    __syncthreads();
+    float2* pw = reinterpret_cast<float2*>(smem);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + kTileThreads * i;
+      if (e < TILEA) pw[TXP == TXA ? e : (e / TXA) * TXP + e % TXA] = make_float2(fa[i], fm[i]);
+    }
+    if (active && nz >= 2) fetch(0);  // after the conversion, whose registers it would otherwise share
     __syncthreads();
   }
   if (!active) return;
-  const int col = (warp + H) * TXA + lane + XOFF - 1;  // tile index of (z = 0, y, x) minus the x tap offset
+  // tile index of (z = 0, y, x) minus the x tap offset (in the pair layout for two-field steps)
+  const int col = (warp + H) * (NF == 2 ? TXP : TXA) + lane + XOFF - 1;
 
   int v = 0;
 #pragma unroll 1
@@ -273,25 +306,39 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
     const float fza = floorf(cza), fya = floorf(cya), fxa = floorf(cxa);
     const float fzb = floorf(czb), fyb = floorf(cyb), fxb = floorf(cxb);
     if (in_halo(fza, fya, fxa) && in_halo(fzb, fyb, fxb)) {
+      constexpr int PT = NF == 2 ? TXP : TXA;
+      const int ba = col + ((v + H + (int)fza) * TY + (int)fya) * PT + (int)fxa;
+      const int bb = col + ((v + 1 + H + (int)fzb) * TY + (int)fyb) * PT + (int)fxb;
       float2 wz[4], wy[4], wx[4];
-      lagrange4v(make_float2(cza - fza, czb - fzb), wz);
-      lagrange4v(make_float2(cya - fya, cyb - fyb), wy);
-      lagrange4v(make_float2(cxa - fxa, cxb - fxb), wx);
-      const int ba = col + ((v + H + (int)fza) * TY + (int)fya) * TXA + (int)fxa;
-      const int bb = col + ((v + 1 + H + (int)fzb) * TY + (int)fyb) * TXA + (int)fxb;
-      const float2 P = interp64<float2>(wz, wy, wx, [&](int o) { return make_float2(sf[ba + o], sf[bb + o]); });
-      float2 S = make_float2(0.f, 0.f);
-      if (NF == 2) S = interp64<float2>(wz, wy, wx, [&](int o) { return make_float2(sg[ba + o], sg[bb + o]); });
-      out[ia] = step_value<MODE>(P.x, S.x, cma, ht);
-      out[ib] = step_value<MODE>(P.y, S.y, cmb, ht);
+      if (NF == 2) {
+        // per voxel, the two fields as one packed pair; the weights carry the voxel's value in both
+        // lanes (computed as a pair of equal arguments), so each lane repeats the scalar arithmetic
+        lagrange4v(vsplat<float2>(cza - fza), wz);
+        lagrange4v(vsplat<float2>(cya - fya), wy);
+        lagrange4v(vsplat<float2>(cxa - fxa), wx);
+        const float2 A = interp64<TXP, float2>(wz, wy, wx, [&](int o) { return sp[ba + o]; });
+        out[ia] = step_value<MODE>(A.x, A.y, cma, ht);
+        lagrange4v(vsplat<float2>(czb - fzb), wz);
+        lagrange4v(vsplat<float2>(cyb - fyb), wy);
+        lagrange4v(vsplat<float2>(cxb - fxb), wx);
+        const float2 B = interp64<TXP, float2>(wz, wy, wx, [&](int o) { return sp[bb + o]; });
+        out[ib] = step_value<MODE>(B.x, B.y, cmb, ht);
+      } else {  // one field: the pair of voxels as one packed pair
+        lagrange4v(make_float2(cza - fza, czb - fzb), wz);
+        lagrange4v(make_float2(cya - fya, cyb - fyb), wy);
+        lagrange4v(make_float2(cxa - fxa, cxb - fxb), wx);
+        const float2 P = interp64<TXA, float2>(wz, wy, wx, [&](int o) { return make_float2(sf[ba + o], sf[bb + o]); });
+        out[ia] = step_value<MODE>(P.x, 0.f, cma, ht);
+        out[ib] = step_value<MODE>(P.y, 0.f, cmb, ht);
+      }
     } else {
-      sl_single<MODE>(f, mu, out, sf, sg, col, ia, bi.bz * BZ + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
-      sl_single<MODE>(f, mu, out, sf, sg, col, ib, bi.bz * BZ + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
+      sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * BZ + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
+      sl_single<MODE>(f, mu, out, sf, col, ib, bi.bz * BZ + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
     }
   }
   if (v < nz) {
     const long long ia = idx0 + v * plane;
-    sl_single<MODE>(f, mu, out, sf, sg, col, ia, bi.bz * BZ + v, v, gy, gx, disp[ia], disp[nv + ia], disp[2 * nv + ia],
+    sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * BZ + v, v, gy, gx, disp[ia], disp[nv + ia], disp[2 * nv + ia],
                     n0, n1, n2, ht);
   }
 }
@@ -386,7 +433,8 @@ template <int MODE>
 cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
                         cudaStream_t st) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
-  const size_t sm = sizeof(float) * TILEA * NF;  // two-field steps: f and f * mu tiles
+  // two-field steps: the f and mu tiles, then the same bytes (plus row padding) as (f, f mu) pairs
+  const size_t sm = NF == 2 ? sizeof(float) * (2 * TILEP > 2 * TILEA ? 2 * TILEP : 2 * TILEA) : sizeof(float) * TILEA;
   void (*kern)(const float*, const float*, const float*, float*, int, int, int, float, int);
   if constexpr (NF == 2) kern = k_sl_tile2<MODE>;
   else kern = k_sl_tile1<MODE>;
@@ -402,7 +450,7 @@ cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const fl
   const bool aligned = ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(mu ? mu : f)) & 15u) == 0;
   const int vec = (g.n[2] % 4 == 0 && g.n[2] >= TXA && g.n[1] >= TY && g.n[0] >= TZ && aligned) ? 1 : 0;
   note_launches(1);
-  kern<<<nb, 256, sm, st>>>(f, mu, disp, out, g.n[0], g.n[1], g.n[2], ht, vec);
+  kern<<<nb, kTileThreads, sm, st>>>(f, mu, disp, out, g.n[0], g.n[1], g.n[2], ht, vec);
   return cudaGetLastError();
 }
 
