@@ -74,6 +74,70 @@ __device__ cx<T>* run_fft(cx<T>* a, cx<T>* b, int N, int B, int ld, const FftPla
   return a;
 }
 
+// ---- forward transform with fused first and last stages (compile-time lengths) ------------------
+template <typename T, int R> __device__ __forceinline__ void dft_r(cx<T>* v) {
+  if constexpr (R == 2) dft2(v);
+  else if constexpr (R == 3) dft3<T>(v);
+  else if constexpr (R == 4) dft4(v);
+  else if constexpr (R == 5) dft5<T>(v);
+  else if constexpr (R == 16) dft16<T>(v);
+  else dft8<T>(v);
+}
+
+// One Stockham stage (length N, radix R, span Ns) over B pencils, from `in` to `out`. The first stage
+// (Ns == 1, all twiddles one) takes its inputs from load(p, i), element i of pencil p, so the staged
+// real data need no separate packing pass; the last stage (Ns * R == N) stores fin(k, value) for
+// frequency index k, so a diagonal scaling needs no separate pass either. With PFAST the first stage
+// gives consecutive threads consecutive pencils (staged tiles whose pencils are adjacent columns).
+template <typename T, int N, int R, int Ns, bool PFAST, typename Load, typename Fin>
+__device__ __forceinline__ void fused_stage(Load& load, Fin& fin, const cx<T>* in, cx<T>* out, int B, int ld,
+                                            const cx<T>* tw) {
+  constexpr int M = N / R;
+  for (int t = threadIdx.x; t < B * M; t += blockDim.x) {
+    const bool pf = PFAST && Ns == 1;
+    const int p = pf ? t % B : t / M, j = pf ? t / B : t - (t / M) * M;
+    const int k = j % Ns;
+    cx<T> v[R];
+    if constexpr (Ns == 1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = load(p, j + r * M);
+    } else {
+      const cx<T>* ip = in + p * ld;
+      const int tstep = k * (N / (Ns * R));
+      v[0] = ip[pd(j)];
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(ip[pd(j + r * M)], tw[r * tstep]);
+    }
+    dft_r<T, R>(v);
+    const int base = (j - k) * R + k;
+    cx<T>* op = out + p * ld;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int q = base + r * Ns;
+      if constexpr (Ns * R == N)
+        op[pd(q)] = fin(q, v[r]);
+      else
+        op[pd(q)] = v[r];
+    }
+  }
+  __syncthreads();
+}
+
+// Forward transform of B pencils read through load(); stage s writes `out` and reads the previous
+// stage's `out`. Returns the buffer holding fin(k, FFT(z)_k).
+template <typename T, int N, int Ns, int MAXR, bool PFAST> struct FusedForward {
+  template <typename Load, typename Fin>
+  __device__ __forceinline__ static cx<T>* run(Load& load, Fin& fin, cx<T>* in, cx<T>* out, int B, int ld,
+                                               const cx<T>* tw) {
+    constexpr int R = ct_next_radix(N / Ns, MAXR);
+    fused_stage<T, N, R, Ns, PFAST>(load, fin, in, out, B, ld, tw);
+    if constexpr (Ns * R >= N)
+      return out;
+    else
+      return FusedForward<T, N, Ns * R, MAXR, PFAST>::run(load, fin, out, in, B, ld, tw);
+  }
+};
+
 // derivative wavenumber k~ of FFT index j of a length-L axis (zero at the Nyquist index)
 template <typename T> __device__ __forceinline__ T ktilde(int j, int L) {
   if (2 * j == L) return T(0);
@@ -184,16 +248,29 @@ k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
   load_tw<T>(sm.tw, twg, L);
   cpa_wait<1>();
   __syncthreads();
-  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-    const int p = idx / L, j = idx - p * L;
-    const T va = (2 * p < nrows) ? sm.raw[(2 * p) * L + j] : T(0);
-    const T vb = (2 * p + 1 < nrows) ? sm.raw[(2 * p + 1) * L + j] : T(0);
-    sm.a[p * ld + pd(j)] = mk<T>(va, vb);
+  cx<T>* r;
+  if constexpr (NC > 0) {  // rows 2p, 2p+1 read straight from the staged block; i k~ applied on the way out
+    const T* raw = sm.raw;
+    auto load = [&](int p, int i) {
+      return mk<T>((2 * p < nrows) ? raw[(2 * p) * L + i] : T(0), (2 * p + 1 < nrows) ? raw[(2 * p + 1) * L + i] : T(0));
+    };
+    auto fin = [&](int k, cx<T> z) {
+      const T kt = ktilde<T>(k, L);
+      return mk<T>(-kt * z.y, -kt * z.x);
+    };
+    r = FusedForward<T, NC, 1, 8, false>::run(load, fin, sm.b, sm.a, B, ld, sm.tw);  // sm.b holds the raw block
+  } else {
+    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+      const int p = idx / L, j = idx - p * L;
+      const T va = (2 * p < nrows) ? sm.raw[(2 * p) * L + j] : T(0);
+      const T vb = (2 * p + 1 < nrows) ? sm.raw[(2 * p + 1) * L + j] : T(0);
+      sm.a[p * ld + pd(j)] = mk<T>(va, vb);
+    }
+    __syncthreads();
+    r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+    mult_ik_conj<T>(r, B, L, ld);
   }
-  __syncthreads();
-  cx<T>* r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
   cx<T>* o = (r == sm.a) ? sm.b : sm.a;
-  mult_ik_conj<T>(r, B, L, ld);
   cx<T>* r2 = run_fft<T, NC, 8>(r, o, L, B, ld, plan, sm.tw);
   cpa_wait<0>();
   __syncthreads();
@@ -230,16 +307,29 @@ k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
   load_tw<T>(sm.tw, twg, L);
   cpa_wait<1>();
   __syncthreads();
-  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-    const int j = idx / B, p = idx - j * B;
-    const T va = (2 * p < valid) ? sm.raw[j * W + 2 * p] : T(0);
-    const T vb = (2 * p + 1 < valid) ? sm.raw[j * W + 2 * p + 1] : T(0);
-    sm.a[p * ld + pd(j)] = mk<T>(va, vb);
+  cx<T>* r;
+  if constexpr (NC > 0) {  // columns 2p, 2p+1 read straight from the staged tile; i k~ applied on the way out
+    const T* raw = sm.raw;
+    auto load = [&](int p, int i) {
+      return mk<T>((2 * p < valid) ? raw[i * W + 2 * p] : T(0), (2 * p + 1 < valid) ? raw[i * W + 2 * p + 1] : T(0));
+    };
+    auto fin = [&](int k, cx<T> z) {
+      const T kt = ktilde<T>(k, L);
+      return mk<T>(-kt * z.y, -kt * z.x);
+    };
+    r = FusedForward<T, NC, 1, 8, true>::run(load, fin, sm.b, sm.a, B, ld, sm.tw);  // sm.b holds the raw tile
+  } else {
+    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+      const int j = idx / B, p = idx - j * B;
+      const T va = (2 * p < valid) ? sm.raw[j * W + 2 * p] : T(0);
+      const T vb = (2 * p + 1 < valid) ? sm.raw[j * W + 2 * p + 1] : T(0);
+      sm.a[p * ld + pd(j)] = mk<T>(va, vb);
+    }
+    __syncthreads();
+    r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
+    mult_ik_conj<T>(r, B, L, ld);
   }
-  __syncthreads();
-  cx<T>* r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
   cx<T>* o = (r == sm.a) ? sm.b : sm.a;
-  mult_ik_conj<T>(r, B, L, ld);
   cx<T>* r2 = run_fft<T, NC, 8>(r, o, L, B, ld, plan, sm.tw);
   cpa_wait<0>();
   __syncthreads();
