@@ -100,10 +100,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // Staged tile: x extent TXA = 40 starting at bx*BX - 4 (16-byte aligned), y and z as before.
 constexpr int TXA = 40, XOFF = 4;
 constexpr int TILEA = TXA * TY * TZ;
-// Two-field steps interleave (f, f mu) into 8-byte pairs with their own row pitch TXP (>= TXA). Padded
-// pitches (41, 44) spread rows and planes of the 64-bit accesses over more banks but measured slower
-// than TXP = TXA on GB300, so the pairs keep the staging layout.
-constexpr int TXP = 40;
+// Two-field steps interleave (f, f mu) into 8-byte pairs with their own row pitch TXP (>= TXA). A
+// half-warp's 64-bit loads cover 16 consecutive pairs; with the row and plane pitches multiples of 16
+// pairs (TXP = 48), lanes whose stencils start on different rows or planes fall on different banks.
+// Measured at 256^3: 48 -> 0.334 ms, 40 -> 0.345 ms, 41 -> 0.361 ms, 44 -> 0.364 ms. 3 CTAs of
+// 75 KB still fit on an SM.
+constexpr int TXP = 48;
 constexpr int TILEP = TXP * TY * TZ;
 
 struct BrickIdx {
