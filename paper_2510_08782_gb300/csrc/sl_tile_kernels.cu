@@ -269,6 +269,16 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
     if (NF == 2) ma = mu[ia], mb = mu[ib];
   };
   if (NF == 1 && active && nz >= 2) fetch(0);
+  if (NF == 2 && active && nz >= 2) {
+    // the first pair's loads follow the tile conversion (which needs the registers): pull their lines
+    // into L2 now, while the tile copies are in flight
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {  // the three displacement components, then mu
+      const float* base = c < 3 ? disp + c * nv + idx0 : mu + idx0;
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(base));
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(base + plane));
+    }
+  }
   asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
   if (NF == 2) {
