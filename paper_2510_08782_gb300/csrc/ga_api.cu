@@ -1,11 +1,12 @@
 // Runtime behind the C ABI of include/ga.h and include/ga_ops.h.
 //
 // One context owns every device buffer of one problem and orders all work on one stream. The
-// gradient evaluation (Eq. (3)) runs as: spectral prologue (F v, regulariser value, mu = div v by
-// 1D derivative passes), RK2 departure points, n_t state steps (all states or checkpoints every K),
-// mismatch and terminal adjoint value, then backwards in time the body force
-// h_t w_j lambda_j grad m_j (one fused FFT-derivative pass per axis) and the adjoint step, and the
-// spectral epilogue g^ = alpha L^ v^ + (P) b^ (optionally fused with s^ = -(P g^)/(alpha L^)).
+// gradient evaluation (Eq. (3)) runs as: the regulariser value 1/2 <v, w> with w = alpha L v (carried
+// by the solver with v; formed by the transform for a caller's v), mu = div v by 1D derivative
+// passes, RK2 departure points, n_t state steps (all states or checkpoints every K), mismatch and
+// terminal adjoint value, then backwards in time the body force h_t w_j lambda_j grad m_j (one fused
+// FFT-derivative pass per axis) and the adjoint step, then g = (P) b + w in real space and, for the
+// solver, s = -(alpha L)^{-1} (P) g and alpha L s by one transform of g.
 // The solver (Alg. 3) drives the line search from the host: each Armijo trial is a state solve whose
 // FP64 objective is read back; the window inner products, the Gram update, the least-squares solve
 // and the combination run on the device.
@@ -313,8 +314,8 @@ template <typename T> struct Engine : EngineBase {
   // w = alpha L v by the transform (Sec. 2.2): used where w is not carried along with v.
   void apply_alphaL(const T* v, T* w) {
     for (int c = 0; c < dim; ++c) r2c(v + c * nv, vh + c * g.nhalf);
-    SpecArgs sa{SPEC_APPLY_ALPHA_L, s, alpha, 0, 0};
-    ck(launch_spectral<T>(g, sa, vh, nullptr, st), "spectral alpha L");
+    SpecArgs sa{SPEC_APPLY_ALPHA_L, s, alpha, 0};
+    ck(launch_spectral<T>(g, sa, vh, st), "spectral alpha L");
     for (int c = 0; c < dim; ++c) c2r(vh + c * g.nhalf, w + c * nv);
   }
   // sum_x v . w into dres[slot]; the regulariser (alpha/2) <v, L v> is h^d/2 times it for w = alpha L v.
@@ -331,12 +332,12 @@ template <typename T> struct Engine : EngineBase {
     for (int c = 0; c < dim; ++c) r2c(gin + c * nv, bh + c * g.nhalf);
     const bool inc = model == GA_MODEL_INCOMPRESSIBLE;
     if (tout && !inc) ck(launch_neg_centered<T>(g, gin, bh, tout, st), "alpha L s");
-    SpecArgs sa{SPEC_PRECOND, s, alpha, inc ? 1 : 0, 0};
-    ck(launch_spectral<T>(g, sa, bh, nullptr, st), "spectral precond");
+    SpecArgs sa{SPEC_PRECOND, s, alpha, inc ? 1 : 0};
+    ck(launch_spectral<T>(g, sa, bh, st), "spectral precond");
     if (tout && inc) {
       ck(cudaMemcpyAsync(vh, bh, sizeof(cx<T>) * g.nhalf * dim, cudaMemcpyDeviceToDevice, st), "copy s^");
-      SpecArgs sl{SPEC_APPLY_ALPHA_L, s, alpha, 0, 0};
-      ck(launch_spectral<T>(g, sl, vh, nullptr, st), "spectral alpha L s");
+      SpecArgs sl{SPEC_APPLY_ALPHA_L, s, alpha, 0};
+      ck(launch_spectral<T>(g, sl, vh, st), "spectral alpha L s");
       for (int c = 0; c < dim; ++c) c2r(vh + c * g.nhalf, tout + c * nv);
     }
     for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, sout + c * nv);
@@ -528,8 +529,8 @@ template <typename T> struct Engine : EngineBase {
     body_force(lam[0]);
     if (model == GA_MODEL_INCOMPRESSIBLE) {  // P b by the transform, in place
       for (int c = 0; c < dim; ++c) r2c(body + c * nv, bh + c * g.nhalf);
-      SpecArgs sp{SPEC_LERAY, s, alpha, 1, 0};
-      ck(launch_spectral<T>(g, sp, bh, nullptr, st), "spectral leray");
+      SpecArgs sp{SPEC_LERAY, s, alpha, 1};
+      ck(launch_spectral<T>(g, sp, bh, st), "spectral leray");
       for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, body + c * nv);
     }
     ck(launch_axpy<T>(gout, body, w, 1.0, vl, st), "g = (P) b + w");
@@ -656,8 +657,8 @@ template <typename T> struct Engine : EngineBase {
     dto_backward(v, lam[0], -hd, dto_buf);  // r = h^d (m(1) - m1) = -h^d lam[0]
     if (model == GA_MODEL_INCOMPRESSIBLE) {
       for (int c = 0; c < dim; ++c) r2c(dto_buf + c * nv, bh + c * g.nhalf);
-      SpecArgs sp{SPEC_LERAY, s, alpha, 1, 0};
-      ck(launch_spectral<T>(g, sp, bh, nullptr, st), "spectral leray");
+      SpecArgs sp{SPEC_LERAY, s, alpha, 1};
+      ck(launch_spectral<T>(g, sp, bh, st), "spectral leray");
       for (int c = 0; c < dim; ++c) c2r(bh + c * g.nhalf, dto_buf + c * nv);
     }
     ck(launch_axpy<T>(gout, wtmp, dto_buf, 1.0 / hd, vl, st), "g = alpha L v + b / h^d");
@@ -1304,8 +1305,8 @@ ga_status ga_op_apply_L(ga_ctx* ctx, const void* v, void* Lv) {
     using T = typename std::remove_reference<decltype(*e.m0)>::type;
     const T* vv = static_cast<const T*>(v);
     for (int c = 0; c < e.dim; ++c) e.r2c(vv + c * e.nv, e.bh + c * e.g.nhalf);
-    SpecArgs sa{SPEC_APPLY_L, e.s, e.alpha, 0, 0};
-    e.ck(launch_spectral<T>(e.g, sa, e.bh, nullptr, e.st), "spectral");
+    SpecArgs sa{SPEC_APPLY_L, e.s, e.alpha, 0};
+    e.ck(launch_spectral<T>(e.g, sa, e.bh, e.st), "spectral");
     for (int c = 0; c < e.dim; ++c) e.c2r(e.bh + c * e.g.nhalf, static_cast<T*>(Lv) + c * e.nv);
     e.ck(cudaStreamSynchronize(e.st), "sync");
   });
@@ -1317,8 +1318,8 @@ ga_status ga_op_leray(ga_ctx* ctx, const void* v, void* pv) {
     using T = typename std::remove_reference<decltype(*e.m0)>::type;
     const T* vv = static_cast<const T*>(v);
     for (int c = 0; c < e.dim; ++c) e.r2c(vv + c * e.nv, e.bh + c * e.g.nhalf);
-    SpecArgs sa{SPEC_LERAY, e.s, e.alpha, 1, 0};
-    e.ck(launch_spectral<T>(e.g, sa, e.bh, nullptr, e.st), "spectral");
+    SpecArgs sa{SPEC_LERAY, e.s, e.alpha, 1};
+    e.ck(launch_spectral<T>(e.g, sa, e.bh, e.st), "spectral");
     for (int c = 0; c < e.dim; ++c) e.c2r(e.bh + c * e.g.nhalf, static_cast<T*>(pv) + c * e.nv);
     e.ck(cudaStreamSynchronize(e.st), "sync");
   });

@@ -38,25 +38,21 @@ template <typename T>
 cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, cudaStream_t st);
 
 // ---- pointwise spectral operators (spectral_kernels.cu) --------------------------------------
-enum SpecMode { SPEC_APPLY_L = 0, SPEC_LERAY = 1, SPEC_PRECOND = 2, SPEC_EPILOGUE = 3, SPEC_APPLY_ALPHA_L = 4 };
+enum SpecMode { SPEC_APPLY_L = 0, SPEC_LERAY = 1, SPEC_PRECOND = 2, SPEC_APPLY_ALPHA_L = 3 };
 struct SpecArgs {
   int mode;
   int s;            // regulariser order
   double alpha;
-  int project;      // apply the Leray projector (incompressible model)
-  int want_s;       // EPILOGUE: also write the preconditioned direction into `v`
+  int project;      // PRECOND: apply the Leray projector first (incompressible model)
 };
-// Fields: x[c] (dim half spectra) updated in place; EPILOGUE: x = b^ in, g^ out; v = v^ in,
-// s^ out (when want_s).
+// x[c] (dim half spectra) updated in place.
 template <typename T>
-cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cx<T>* v, cudaStream_t st);
+cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cudaStream_t st);
 // partial[b] = sum over the half spectrum (weights 1/2) of |k|^{2s} |v^_c|^2 summed over c.
 // t = -(g - mean(g)) per component (= alpha L s for s = -(alpha L)^{-1} g), the means taken from the
 // zero modes of gh, the half spectrum of g
 template <typename T>
 cudaError_t launch_neg_centered(const Grid& g, const T* gv, const cx<T>* gh, T* t, cudaStream_t st);
-template <typename T>
-cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partial, cudaStream_t st);
 
 // ---- semi-Lagrangian transport (sl_kernels.cu) -----------------------------------------------
 // Displacements (grid units) of the RK2 departure points X- (xm) and, when both != 0, X+ (xp).

@@ -67,7 +67,7 @@ __device__ __forceinline__ void leray(const KVec<T>& kv, int dim, cx<T>* x) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_spectral(Grid g, SpecArgs a, cx<T>* __restrict__ x, cx<T>* __restrict__ v) {
+k_spectral(Grid g, SpecArgs a, cx<T>* __restrict__ x) {
   const long long nh = g.nhalf;
   const int dim = g.dim;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nh;
@@ -92,19 +92,6 @@ k_spectral(Grid g, SpecArgs a, cx<T>* __restrict__ x, cx<T>* __restrict__ v) {
       for (int c = 0; c < dim; ++c) x[c * nh + idx] = cscale(xv[c], (T)inv);
       continue;
     }
-    // SPEC_EPILOGUE: g^ = alpha L^ v^ + (P) b^ ; optionally s^ = -(P g^) / (alpha L^_fix)
-    if (a.project) leray<T>(kv, dim, xv);
-    cx<T> gv[3];
-    const T aL = (T)(a.alpha * L);
-    for (int c = 0; c < dim; ++c) {
-      const cx<T> vv = v[c * nh + idx];
-      gv[c] = mk<T>(aL * vv.x + xv[c].x, aL * vv.y + xv[c].y);
-      x[c * nh + idx] = gv[c];
-    }
-    if (a.want_s) {
-      if (a.project) leray<T>(kv, dim, gv);
-      for (int c = 0; c < dim; ++c) v[c * nh + idx] = cscale(gv[c], (T)inv);
-    }
   }
 }
 
@@ -121,57 +108,14 @@ k_neg_centered(const T* __restrict__ gv, const cx<T>* __restrict__ gh, T* __rest
   }
 }
 
-// sum over the half spectrum of w(k) |k|^{2s} |v^_c(k)|^2 (w = 1 on the k2 = 0 and Nyquist planes,
-// 2 elsewhere). Terms are formed in the element type; each thread accumulates them in a compensated
-// (double-float for FP32) sum, CTAs combine in FP64.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_reg_sum(Grid g, int s, const cx<T>* __restrict__ vh, double* __restrict__ partial) {
-  const long long nh = g.nhalf;
-  T hi = T(0), lo = T(0);
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nh;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const KVec<T> kv = kvec_of<T>(g, idx);
-    const int i2 = (int)(idx % g.n2h);
-    const T w = (i2 == 0 || 2 * i2 == g.n[2]) ? T(1) : T(2);
-    T e = T(0);
-    for (int c = 0; c < g.dim; ++c) {
-      const cx<T> z = vh[c * nh + idx];
-      e += z.x * z.x + z.y * z.y;
-    }
-    const T term = w * symbol_L<T>(kv, s) * e;
-    const T t = hi + term;  // two-sum
-    const T bb = t - hi;
-    lo += (hi - (t - bb)) + (term - bb);
-    hi = t;
-  }
-  double acc = (double)hi + (double)lo;
-  __shared__ double red[kThreads / 32];
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double r = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
-    for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
-    if (threadIdx.x == 0) partial[blockIdx.x] = r;
-  }
-}
-
 }  // namespace
 
 template <typename T>
-cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cx<T>* v, cudaStream_t st) {
+cudaError_t launch_spectral(const Grid& g, const SpecArgs& a, cx<T>* x, cudaStream_t st) {
   long long blocks = (g.nhalf + kThreads - 1) / kThreads;
   if (blocks > 152 * 8) blocks = 152 * 8;
   note_launches(1);
-  k_spectral<T><<<(unsigned)blocks, kThreads, 0, st>>>(g, a, x, v);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_reg_sum(const Grid& g, int s, const cx<T>* vh, double* partial, cudaStream_t st) {
-  note_launches(1);
-  k_reg_sum<T><<<kRedBlocks, kThreads, 0, st>>>(g, s, vh, partial);
+  k_spectral<T><<<(unsigned)blocks, kThreads, 0, st>>>(g, a, x);
   return cudaGetLastError();
 }
 
@@ -184,10 +128,8 @@ cudaError_t launch_neg_centered(const Grid& g, const T* gv, const cx<T>* gh, T* 
   return cudaGetLastError();
 }
 
-template cudaError_t launch_spectral<float>(const Grid&, const SpecArgs&, cx<float>*, cx<float>*, cudaStream_t);
-template cudaError_t launch_spectral<double>(const Grid&, const SpecArgs&, cx<double>*, cx<double>*, cudaStream_t);
-template cudaError_t launch_reg_sum<float>(const Grid&, int, const cx<float>*, double*, cudaStream_t);
-template cudaError_t launch_reg_sum<double>(const Grid&, int, const cx<double>*, double*, cudaStream_t);
+template cudaError_t launch_spectral<float>(const Grid&, const SpecArgs&, cx<float>*, cudaStream_t);
+template cudaError_t launch_spectral<double>(const Grid&, const SpecArgs&, cx<double>*, cudaStream_t);
 template cudaError_t launch_neg_centered<float>(const Grid&, const float*, const cx<float>*, float*, cudaStream_t);
 template cudaError_t launch_neg_centered<double>(const Grid&, const double*, const cx<double>*, double*, cudaStream_t);
 
