@@ -268,6 +268,9 @@ def run_sweep(args):
     return 0
 
 
+GRAPH_MODES = {"off": False, "replay": True, "device": "device"}
+
+
 def run_batch(args):
     """Batched form: 32 independent 3D advection problems with grids drawn from {64,96,128,160}^3,
     n_t = 4, H1, alpha in {1e-2, 1e-3}, GA-NGMRES(5; 4, 2) to rel-grad 1e-2, FP32 fields. One step =
@@ -298,7 +301,7 @@ def run_batch(args):
         torch.cuda.synchronize()  # pooled streams do not order themselves after the default stream
         P = ga.Problem(d0, d1, nt=w["nt"], model="advection", reg_order=1, alpha=w["alpha"],
                        prec="mixed", window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2, stream=st.cuda_stream,
-                       graphs=args.graphs)
+                       graphs=GRAPH_MODES[args.graphs])
         ctxs.append(P)
         vs.append(torch.zeros((3,) + tuple(w["n"]), dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
@@ -334,8 +337,10 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch: 32 problems, grids from {64,96,128,160}^3, nt=4, H1, alpha in {1e-2,1e-3}, "
-                                   "GA-NGMRES(5;4,2) to rel-grad 1e-2, one stream per problem",
-                       "graphs": bool(args.graphs)},
+                                   "GA-NGMRES(5;4,2) to rel-grad 1e-2, " +
+                                   ("the whole batch one CUDA graph launch" if args.graphs == "device"
+                                    else "one stream per problem"),
+                       "graphs": args.graphs},
             "sequential_s_per_batch": seq,
             "per_problem": [{"n": int(w["n"][0]), "alpha": w["alpha"], "iters": st.iters,
                              "grad_evals": st.grad_evals, "converged": bool(st.converged)}
@@ -352,6 +357,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tts", action="store_true")
+    ap.add_argument("--no-device-tts", action="store_true",
+                    help="skip the device-driven (one graph launch) time-to-solution")
     ap.add_argument("--prof-class", type=int, default=PROF_SL_FWD)
     ap.add_argument("--grid", type=int, default=N, help="grid size (default 256; smaller only for smoke runs)")
     ap.add_argument("--sweep-parts", default="hyper,alpha,mesh",
@@ -361,8 +368,9 @@ def main():
                     help="--workload sweep: tolerance of the hyperparameter and alpha parts (mesh: 1e-3)")
     ap.add_argument("--workload", default="cont3d256", choices=["cont3d256", "batch", "sweep"],
                     help="cont3d256 (default) or batch: 32 independent advection problems of uneven size")
-    ap.add_argument("--graphs", action="store_true",
-                    help="--workload batch: replay each problem's repeated evaluations from CUDA graphs")
+    ap.add_argument("--graphs", nargs="?", const="replay", default="off", choices=["off", "replay", "device"],
+                    help="--workload batch: 'replay' each problem's repeated evaluations from CUDA graphs, or "
+                         "'device': the whole batch as one graph launch with the solver's decisions on the device")
     ap.add_argument("--dto", action="store_true",
                     help="also time the discretise-then-optimise gradient (advection transport, same data)")
     ap.add_argument("--compare-methods", action="store_true",
@@ -432,6 +440,7 @@ def main():
     clocks = sampler.stop()
     prof_ms, prof_n = ga.ga_prof_stop(P.ctx)
     launches = ga.ga_kernel_launches() - launches0
+    deriv_tiles = ga.ga_op_get_tiles(P.ctx, 3)  # pencil pairs per CTA chosen by the setup autotuner
     ms = e0.elapsed_time(e1)
     grad_evals = st.grad_evals
     ms_max, total_evals = aggregate_over_ranks(ms, grad_evals)
@@ -509,6 +518,33 @@ def main():
                        "det_std": float(jd.std()), "max_displacement_cells": float(u_def.abs().max()),
                        "ms": def_ms}
         del u_def, j_def, jd
+
+    # ---- the same solve device-driven: one CUDA graph launch, decisions on the device (graphs = 2) ----
+    tts_dev = None
+    if tts is not None and not args.no_device_tts:
+        Pd = ga.Problem(m0, m1, prec="mixed", graphs="device", **SETTINGS)
+        vd = torch.zeros_like(v)
+        t0 = time.perf_counter()
+        try:
+            Pd.solve(vd)  # the first call records and instantiates the graph
+            torch.cuda.synchronize()
+            first_s = time.perf_counter() - t0
+            vd.zero_()
+            barrier()
+            t0 = time.perf_counter()
+            sd, _ = Pd.solve(vd)
+            err = None
+        except ga.GaError as e:
+            first_s, err = None, str(e)
+            sd = Pd.stats()
+        torch.cuda.synchronize()
+        tts_dev = {"tts_s": time.perf_counter() - t0, "iters": sd.iters, "converged": bool(sd.converged),
+                   "rel_grad_inf": sd.rel_grad_inf, "grad_evals": sd.grad_evals, "obj_evals": sd.obj_evals,
+                   "first_call_s": first_s, "identical_to_host_driven": bool(torch.equal(vd, v_sol)),
+                   "error": err}
+        Pd.close()
+        del Pd, vd
+        torch.cuda.empty_cache()
 
     # ---- the same solve on the FP64 GPU path (optional) ----
     fp64 = None
@@ -640,7 +676,8 @@ def main():
                            "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "tts": tts, "fp64_tts": fp64, "methods_tts": methods, "deformation": deformation, "dto": dto_res, "grad_only_evals_per_s": grad_only,
+                "deriv_tiles_zyx": deriv_tiles,
+                "clocks": clocks, "tts": tts, "tts_device": tts_dev, "fp64_tts": fp64, "methods_tts": methods, "deformation": deformation, "dto": dto_res, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in
                                                                        ("iters", "obj_evals", "rel_grad_inf", "obj",
                                                                         "rho_mem")}}

@@ -80,10 +80,20 @@ typedef struct {
   int variant;         /* 1: FP step when mod(k, sigma+tau) >= sigma (GA-NGMRES);
                           2: FP step when mod(k, sigma+tau) < tau (aNGMRES(w)[sigma]-FP[tau]) */
   int method;          /* ga_method                                                         */
-  int graphs;          /* 1: capture the evaluations the solver repeats (line-search objective,
-                          gradients) into CUDA graphs on the context stream and replay them; 0: launch
-                          kernel by kernel. Results are the same; graphs cut launch overhead on small
-                          grids and cost 3 vector fields of device memory.                           */
+  int graphs;          /* 0: launch kernel by kernel, the host taking the line-search and step
+                          decisions (one synchronisation per evaluation).
+                          1: as 0, but the evaluations the solver repeats (line-search objective,
+                          gradients) are captured into CUDA graphs and replayed; costs 3 vector fields
+                          of device memory.
+                          2: device-driven: ga_solve is one CUDA graph launch (and ga_solve_batch one
+                          launch for all problems when every context uses 2). Conditional graph
+                          nodes loop over the iterations and the line-search trials and choose the
+                          kind of step from control kernels that take the host's decisions on the
+                          device; the host synchronises once per call. GA-NGMRES and RPGD only
+                          (GA_ERR_ARG with GA-AA). ga_step runs one iteration of the same graph.
+                          t_grad_ms then holds the device time of whole runs and t_obj_ms stays 0.
+                          After a failed run the next ga_step starts afresh from its v_inout.
+                          All three give the same iterates and counters, bit for bit.             */
 } ga_solver_opts;
 
 /* Per-context counters and last-iterate metrics (the columns of the paper's tables, Sec. 3.3). */
@@ -158,10 +168,13 @@ ga_status ga_solve(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats);
 /* Forget the iteration state (k = 0, empty window, rho memory = 1); data stay. */
 ga_status ga_reset(ga_ctx* ctx);
 
-/* Solve `count` independent problems, each with its own context (the batched form of the solver):
- * the problems are driven concurrently by host workers, each on its own context's stream, so their
- * kernels overlap on the GPU; give every context its own stream for the overlap to happen. Contexts
- * must be distinct. v[i] is problem i's v_inout (all in memory `mem`); stats[i] (may be NULL)
+/* Solve `count` independent problems, each with its own context (the batched form of the solver).
+ * When every context was set up with graphs = 2, all the solves are chains of one CUDA graph,
+ * launched once (on a library stream ordered after each context's stream and before its results are
+ * read); the graph is kept for the next call with the same list of contexts and dropped when one of
+ * them is destroyed. Otherwise the problems are driven concurrently by host workers, each on its own
+ * context's stream, so their kernels overlap on the GPU; give every context its own stream for the
+ * overlap to happen. Contexts must be distinct. v[i] is problem i's v_inout (all in memory `mem`); stats[i] (may be NULL)
  * receives its statistics. Returns the first non-OK status other than GA_ERR_NOT_CONVERGED in
  * problem order, else GA_ERR_NOT_CONVERGED if any problem hit its cap, else GA_OK. */
 ga_status ga_solve_batch(int count, ga_ctx* const* ctxs, void* const* v, int mem, ga_stats* stats);

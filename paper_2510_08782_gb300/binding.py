@@ -80,6 +80,8 @@ _SIGS = {
     "ga_op_body_force": ([_vp, _vp, _vp, _vp], _c_int),
     "ga_op_deriv": ([_vp, _vp, _c_int, _vp], _c_int),
     "ga_op_div": ([_vp, _vp, _vp], _c_int),
+    "ga_op_get_tiles": ([_vp, ctypes.POINTER(_c_int)], _c_int),
+    "ga_op_set_tiles": ([_vp, ctypes.POINTER(_c_int)], _c_int),
     "ga_op_fft_r2c": ([_vp, _vp, _vp], _c_int),
     "ga_op_fft_c2r": ([_vp, _vp, _vp], _c_int),
     "ga_op_apply_L": ([_vp, _vp, _vp], _c_int),
@@ -217,6 +219,12 @@ def ga_step(ctx, dtype, v):
     return stt
 
 
+def ga_get_stats(ctx):
+    stt = Stats()
+    _check(lib().ga_get_stats(ctx, ctypes.byref(stt)), ctx)
+    return stt
+
+
 def ga_solve(ctx, dtype, v):
     (pv,), mem = _ptrs(dtype, v)
     stt = Stats()
@@ -288,6 +296,18 @@ def ga_op_body_force(ctx, dtype, v, lam1, b):
 def ga_op_deriv(ctx, dtype, f, axis, df):
     pf, pd = _dev(dtype, f, df)
     _check(lib().ga_op_deriv(ctx, pf, int(axis), pd), ctx)
+
+
+def ga_op_get_tiles(ctx, dim):
+    """Pencil pairs per CTA of the FFT-derivative pass along each axis (chosen by the autotuner)."""
+    arr = (_c_int * dim)()
+    _check(lib().ga_op_get_tiles(ctx, arr), ctx)
+    return list(arr)
+
+
+def ga_op_set_tiles(ctx, pencils):
+    arr = (_c_int * len(pencils))(*[int(p) for p in pencils])
+    _check(lib().ga_op_set_tiles(ctx, arr), ctx)
 
 
 def ga_op_div(ctx, dtype, v, mu):
@@ -393,7 +413,12 @@ class Problem:
         if method not in methods:
             raise ValueError(f"method must be one of {sorted(methods)}")
         o.method = methods[method]
-        o.graphs = 1 if graphs else 0
+        # graphs: False/0 kernel by kernel; True/1 evaluations replayed from CUDA graphs; "device"/2 the
+        # whole solve as one graph, its line search and step decisions taken on the device
+        graph_modes = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "device": 2}
+        if graphs not in graph_modes:
+            raise ValueError("graphs must be False, True or 'device'")
+        o.graphs = graph_modes[graphs]
         self.desc, self.opts = d, o
         self.ctx = ga_setup(d, o, m0, m1, stream)
 
@@ -433,6 +458,10 @@ class Problem:
 
     def reset(self):
         ga_reset(self.ctx)
+
+    def stats(self):
+        """Counters and last-iterate metrics of the context (also after a failed call)."""
+        return ga_get_stats(self.ctx)
 
     def transport(self, v, m1_out):
         ga_transport(self.ctx, self.dtype, v, m1_out)

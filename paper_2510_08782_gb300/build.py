@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libga_gb300.so")
 SOURCES = ["ga_api.cu", "fft_kernels.cu", "sl_kernels.cu", "sl_tile_kernels.cu", "spectral_kernels.cu",
-           "reduce_kernels.cu", "noalloc.cu", "dto_kernels.cu"]
+           "reduce_kernels.cu", "noalloc.cu", "dto_kernels.cu",
+           "control_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -547,7 +547,7 @@ cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const 
     if (accumulate) return cudaSuccess;
     return cudaMemsetAsync(out, 0, sizeof(T) * g.nvox, st);
   }
-  int B = deriv_batch<T>(L);
+  int B = ft.deriv_pencils[axis] > 0 ? ft.deriv_pencils[axis] : deriv_batch<T>(L);
   const int ld = lead_dim(L);
   const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   const bool ptrs16 = al(f) && al(out) && (!mult || al(mult));
@@ -679,7 +679,14 @@ cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, c
   });
 }
 
+template <typename T> int deriv_default_pencils(int L) { return deriv_batch<T>(L); }
+template <typename T> bool deriv_pencils_fit(int L, int B) {
+  return B >= 1 && deriv_smem_bytes<T>(L, B) <= (size_t)smem_optin_max();
+}
+
 #define GA_INST(T)                                                                                  \
+  template int deriv_default_pencils<T>(int);                                                       \
+  template bool deriv_pencils_fit<T>(int, int);                                                     \
   template cudaError_t launch_deriv<T>(const Grid&, const FftTables<T>&, int, const T*, const T*, T*, T, \
                                        bool, cudaStream_t);                                          \
   template cudaError_t launch_r2c<T>(const Grid&, const FftTables<T>&, const T*, cx<T>*, cudaStream_t); \

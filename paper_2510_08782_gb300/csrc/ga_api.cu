@@ -14,12 +14,15 @@
 
 #include <algorithm>
 #include <atomic>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <type_traits>
@@ -131,6 +134,10 @@ template <typename T> struct Engine : EngineBase {
     for (auto ge : gexec)
       if (ge) cudaGraphExecDestroy(ge);
     if (gst) cudaStreamDestroy(gst);
+    if (rexec) cudaGraphExecDestroy(rexec);
+    for (auto cs : cap)
+      if (cs) cudaStreamDestroy(cs);
+    if (hctl) cudaFreeHost(hctl);
   }
 
   void ck(cudaError_t e, const char* what) {
@@ -226,13 +233,29 @@ template <typename T> struct Engine : EngineBase {
     // solver pools: window (w+1) + trial q + one more, for iterates and gradients. An iterate buffer
     // holds v in [0, vl) and w = alpha L v in [vl, 2 vl); S holds s and alpha L s the same way.
     W1 = c->opts.window + 1;
-    for (int i = 0; i < W1 + 2; ++i) {
-      vfree.push_back(dalloc<T>(2 * vl));
-      gfree.push_back(dalloc<T>(vl));
+    resident = c->opts.graphs == 2;
+    if (resident) {  // the same memory as the pools, in fixed roles (see the device-driven solve below)
+      VC = dalloc<T>(2 * vl);
+      Q = dalloc<T>(2 * vl);
+      GC = dalloc<T>(vl);
+      GQ = dalloc<T>(vl);
+      RV = dalloc<T>((long long)W1 * 2 * vl);
+      RG = dalloc<T>((long long)W1 * vl);
+      dctl = dalloc<ResCtl>(1);
+      void* hp = nullptr;
+      ck(cudaMallocHost(&hp, sizeof(ResCtl)), "cudaMallocHost");
+      hctl = static_cast<ResCtl*>(hp);
+      std::memset(hctl, 0, sizeof(ResCtl));
+      for (auto& cs : cap) ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    } else {
+      for (int i = 0; i < W1 + 2; ++i) {
+        vfree.push_back(dalloc<T>(2 * vl));
+        gfree.push_back(dalloc<T>(vl));
+      }
     }
     S = dalloc<T>(2 * vl);
     wtmp = dalloc<T>(vl);
-    graphs = c->opts.graphs != 0;
+    graphs = c->opts.graphs == 1;
     if (graphs) {
       gin = dalloc<T>(2 * vl);
       gbuf = dalloc<T>(vl);
@@ -242,7 +265,53 @@ template <typename T> struct Engine : EngineBase {
     dM = dalloc<double>((long long)W1 * W1);
     dbeta = dalloc<double>(kMaxWin + 4);
     ck(cudaMemsetAsync(dM, 0, sizeof(double) * W1 * W1, st), "memset");
+    autotune_tiles();
     ck(cudaStreamSynchronize(st), "setup sync");
+  }
+
+  // ---- tile autotuner --------------------------------------------------------------------------
+  // The FFT-derivative passes (two thirds of the body force's launches) take their tile shape, the
+  // number of pencils a CTA transforms, from timing: for each axis the default and its half and double
+  // are run on this context's own fields (m0 differentiated, times m1, accumulated into a scratch
+  // field), the fastest kept. Choices are cached per (precision, grid) for the process. Each pencil is
+  // transformed on its own, so no result depends on the choice.
+  void autotune_tiles() {
+    static std::mutex mu;
+    static std::map<std::vector<int>, std::array<int, 3>> cache;
+    const std::vector<int> key = {(int)sizeof(T), g.n[0], g.n[1], g.n[2]};
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) {
+        for (int a = 0; a < 3; ++a) ft.deriv_pencils[a] = it->second[a];
+        return;
+      }
+    }
+    std::array<int, 3> best = {0, 0, 0};
+    for (int a = 3 - dim; a < 3; ++a) {
+      const int L = g.n[a];
+      if (L == 1) continue;
+      const int b0 = deriv_default_pencils<T>(L);
+      float best_ms = 0.f;
+      for (int cand : {b0, b0 / 2, 2 * b0}) {
+        if (!deriv_pencils_fit<T>(L, cand)) continue;
+        ft.deriv_pencils[a] = cand;
+        ck(launch_deriv<T>(g, ft, a, m0, m1, tmp[0], T(1), false, st), "tuning pass");  // loads the kernel
+        ck(cudaEventRecord(ev[0], st), "event");
+        for (int r = 0; r < 3; ++r) ck(launch_deriv<T>(g, ft, a, m0, m1, tmp[0], T(1), true, st), "tuning pass");
+        ck(cudaEventRecord(ev[1], st), "event");
+        ck(cudaEventSynchronize(ev[1]), "event sync");
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
+        if (best[a] == 0 || ms < best_ms) {
+          best[a] = cand;
+          best_ms = ms;
+        }
+      }
+      ft.deriv_pencils[a] = best[a];
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache.emplace(key, best);
   }
 
   // ---- profiling hooks ------------------------------------------------------------------------
@@ -382,8 +451,10 @@ template <typename T> struct Engine : EngineBase {
   }
 
   void issue_results(int count) {
+    if (!host_results) return;  // recorded into the device-driven solve's graph: results stay on the device
     ck(cudaMemcpyAsync(hres, dres, sizeof(double) * count, cudaMemcpyDeviceToHost, st), "result copy");
   }
+  bool host_results = true;
   void wait_results() {
     ck(cudaStreamSynchronize(st), "sync");
     prof_flush();
@@ -681,6 +752,252 @@ template <typename T> struct Engine : EngineBase {
   }
 
   // ---- solver (Alg. 3) -----------------------------------------------------------------------------
+  // ---- device-driven solve (ga_solver_opts.graphs == 2) ------------------------------------------
+  // Fixed roles: the iterate v and w = alpha L v in VC with its gradient in GC; the line-search trial q
+  // (and alpha L q) in Q with its gradient in GQ; the window in a ring of W1 slots (RV: v and w, RG: g)
+  // indexed on the device (ResCtl). One graph holds a whole solve:
+  //   IF (!started) { w = alpha L v; g, s at v; push }         (start of Alg. 3)
+  //   WHILE (k < kmax, no failure, not converged) {
+  //     <g, s>;  WHILE (trial rejected) { q = v + rho s; obj(q) keeping its trajectory; Armijo }
+  //     SWITCH (step kind) { 0: g, s at q; v = q  |  1: g at q; window least squares; v = q + sum
+  //       beta_i (q - v_i); g, s at v }
+  //     push (v, g) into the window; k += 1; stop test }
+  // and its kernels are the ones the host-driven solver launches, in the same order on the same data, so
+  // both give the same iterates bit for bit.
+  bool resident = false, rstarted = false;
+  ResCtl* dctl = nullptr;
+  ResCtl* hctl = nullptr;  // pinned copy of *dctl as of the last launch
+  T *VC = nullptr, *GC = nullptr, *Q = nullptr, *GQ = nullptr, *RV = nullptr, *RG = nullptr;
+  cudaStream_t cap[3] = {};  // capture streams, one per nesting level of the graph
+  cudaGraphExec_t rexec = nullptr;
+  // kernels recorded per body of the graph (for the launch count of a run)
+  long long rk_fixed = 0, rk_start = 0, rk_iter = 0, rk_trial = 0, rk_fp = 0, rk_ga = 0;
+
+  cudaGraph_t capturing_graph() {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t gr = nullptr;
+    ck(cudaStreamGetCaptureInfo(st, &cst, nullptr, &gr, nullptr, nullptr, nullptr), "capture info");
+    return gr;
+  }
+  cudaGraphConditionalHandle new_handle() {
+    cudaGraphConditionalHandle h;
+    ck(cudaGraphConditionalHandleCreate(&h, capturing_graph(), 0, 0), "conditional handle");
+    return h;
+  }
+  // Appends a conditional node after the work captured so far on st; returns its body graphs.
+  cudaGraph_t* add_conditional(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, unsigned size) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t gr = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    ck(cudaStreamGetCaptureInfo(st, &cst, nullptr, &gr, &deps, nullptr, &nd), "capture info");
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    cudaGraphNode_t node;
+    ck(cudaGraphAddNode(&node, gr, deps, nullptr, nd, &p), "conditional node");
+    ck(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+       "capture dependencies");
+    return p.conditional.phGraph_out;
+  }
+  // Records f() into graph `into` (a new chain with no dependencies) on capture stream `lvl`; returns
+  // the number of kernels recorded.
+  template <typename F> long long capture_to(cudaGraph_t into, int lvl, F&& f) {
+    cudaStream_t cs = cap[lvl];
+    const long long c0 = t_launches;
+    ck(cudaStreamBeginCaptureToGraph(cs, into, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+       "begin capture");
+    cudaStream_t saved = st;
+    st = cs;
+    try {
+      f();
+    } catch (...) {
+      st = saved;
+      cudaGraph_t gr = nullptr;
+      cudaStreamEndCapture(cs, &gr);
+      throw;
+    }
+    st = saved;
+    cudaGraph_t gr = nullptr;
+    ck(cudaStreamEndCapture(cs, &gr), "end capture");
+    return t_launches - c0;
+  }
+
+  void res_push(int iteration, cudaGraphConditionalHandle h_iter) {
+    ck(launch_ring_store<T>(RV, 2 * vl, dctl, W1, VC, 2 * vl, st), "ring v");
+    ck(launch_ring_store<T>(RG, vl, dctl, W1, GC, vl, st), "ring g");
+    ck(launch_dots_ring<T>(GC, GC, RG, vl, dctl, W1, 1, vl, dpart, dres + kResDots, st), "window dots");
+    ck(launch_gram_push_ring(dM, W1, dctl, dres + kResDots, st), "gram push");
+    ck(launch_res_pushed(dctl, iteration, h_iter, st), "window push");
+  }
+
+  // Adds this problem's whole solve to `top` as an independent chain of nodes.
+  void add_resident(cudaGraph_t top) {
+    const int saved_prof = prof_class;
+    prof_class = -1;
+    host_results = false;
+    const long long c0 = t_launches;
+    try {
+      long long inner = 0;
+      capture_to(top, 0, [&] {
+        const cudaGraphConditionalHandle h_start = new_handle(), h_iter = new_handle();
+        ck(launch_res_enter(dctl, h_start, st), "enter");
+        cudaGraph_t* b = add_conditional(h_start, cudaGraphCondTypeIf, 1);
+        rk_start = capture_to(b[0], 1, [&] {
+          apply_alphaL(VC, VC + vl);
+          enqueue_gradient(VC, VC + vl, GC, S, false);
+          ck(launch_res_grad(dctl, dres, RES_GRAD_START, st), "start");
+          res_push(0, 0);
+        });
+        ck(launch_res_loop_cond(dctl, h_iter, st), "loop condition");
+        cudaGraph_t* l = add_conditional(h_iter, cudaGraphCondTypeWhile, 1);
+        rk_iter = capture_to(l[0], 1, [&] {
+          const T* bl[1] = {S};
+          ck(launch_dots<T>(GC, bl, 1, vl, dpart, dres + 8, st), "<g, s>");
+          const cudaGraphConditionalHandle h_ls = new_handle();
+          ck(launch_res_ls_begin(dctl, dres + 8, h_ls, st), "line search");
+          cudaGraph_t* lb = add_conditional(h_ls, cudaGraphCondTypeWhile, 1);
+          rk_trial = capture_to(lb[0], 2, [&] {
+            ck(launch_axpy_dev<T>(Q, VC, S, &dctl->rho, 2 * vl, st), "q = v + rho s");
+            enqueue_objective(Q, Q + vl, true);
+            ck(launch_res_ls_check(dctl, dres, h_ls, st), "Armijo test");
+          });
+          const cudaGraphConditionalHandle h_sw = new_handle();
+          ck(launch_res_branch(dctl, h_sw, st), "step kind");
+          cudaGraph_t* sw = add_conditional(h_sw, cudaGraphCondTypeSwitch, 2);
+          rk_fp = capture_to(sw[0], 2, [&] {  // fixed-point step: v <- q
+            enqueue_gradient(Q, Q + vl, GQ, S, true);
+            ck(launch_res_grad(dctl, dres, RES_GRAD_ACCEPTED, st), "gradient");
+            ck(cudaMemcpyAsync(VC, Q, sizeof(T) * 2 * vl, cudaMemcpyDeviceToDevice, st), "copy q");
+            ck(cudaMemcpyAsync(GC, GQ, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy g");
+          });
+          rk_ga = capture_to(sw[1], 2, [&] {  // NGMRES step: v <- q + sum_i beta_i (q - v_i)
+            enqueue_gradient(Q, Q + vl, GQ, nullptr, true);
+            ck(launch_res_grad(dctl, dres, RES_GRAD_TRIAL, st), "gradient");
+            ck(launch_dots_ring<T>(GQ, GQ, RG, vl, dctl, W1, 0, vl, dpart, dres + kResDots, st), "lsq dots");
+            ck(launch_lsq_ring(dctl, W1, dres + kResDots, dM, dbeta, dres + kResLsq, st), "lsq");
+            ck(launch_combine_ring<T>(VC, Q, RV, 2 * vl, dctl, W1, dbeta, 2 * vl, st), "combine");
+            enqueue_gradient(VC, VC + vl, GC, S, false);
+            ck(launch_res_grad(dctl, dres, RES_GRAD_COMBINED, st), "gradient");
+          });
+          res_push(1, h_iter);
+        });
+        inner = rk_start + rk_iter;
+      });
+      rk_iter -= rk_trial + rk_fp + rk_ga;  // kernels of an iteration outside its nested bodies
+      rk_fixed = (t_launches - c0) - inner;  // enter and loop condition
+    } catch (...) {
+      host_results = true;
+      prof_class = saved_prof;
+      note_launches((int)-(t_launches - c0));
+      throw;
+    }
+    host_results = true;
+    prof_class = saved_prof;
+    note_launches((int)-(t_launches - c0));  // recorded, not launched
+  }
+
+  // Host side of a run: parameters into the pinned copy (a fresh run also clears the state, so the
+  // graph starts the solve from VC), then copied to the device on st.
+  void res_prepare(bool fresh, int kmax, int stop) {
+    if (fresh) std::memset(hctl, 0, sizeof(ResCtl));
+    const ga_solver_opts& o = ctx->opts;
+    hctl->armijo_c = o.armijo_c;
+    hctl->rel_tol = o.rel_tol;
+    hctl->hd = hd;
+    hctl->max_backtracks = o.max_backtracks;
+    hctl->sigma = o.sigma;
+    hctl->tau = o.tau;
+    hctl->variant = o.variant;
+    hctl->method = o.method;
+    hctl->W1 = W1;
+    hctl->kmax = kmax;
+    hctl->stop_on_converged = stop;
+    res_before = *hctl;
+    ck(cudaMemcpyAsync(dctl, hctl, sizeof(ResCtl), cudaMemcpyHostToDevice, st), "control upload");
+  }
+  ResCtl res_before{};
+  void res_fetch() { ck(cudaMemcpyAsync(hctl, dctl, sizeof(ResCtl), cudaMemcpyDeviceToHost, st), "control download"); }
+  // After the stream has synchronised: statistics, launch count and status of the run.
+  // `ms`: device time of the run (evaluations and control are not timed apart; added to t_grad_ms).
+  void res_finish(float ms) {
+    const ResCtl& c = *hctl;
+    const ResCtl& b = res_before;
+    const long long iters = c.k - b.k, trials = c.ls_trials - b.ls_trials, fps = c.fp_steps - b.fp_steps;
+    long long n = rk_fixed + (b.started ? 0 : rk_start) + iters * rk_iter + trials * rk_trial + fps * rk_fp +
+                  (iters - fps) * rk_ga;
+    if (c.status != 0 && c.started) {  // the failed iteration ran its kernels but did not count itself
+      n += rk_iter;
+      if (c.branch == 0) n += rk_fp;
+      if (c.branch == 1) n += rk_ga;
+    }
+    note_launches((int)n);
+    ga_stats& o = ctx->stats;
+    if (!b.started) o = ga_stats{};
+    o.t_grad_ms += ms;
+    o.iters = c.k;
+    o.grad_evals = (int)c.grad_evals;
+    o.obj_evals = (int)c.obj_evals;
+    o.pde_solves = (int)c.pde_solves;
+    o.ls_trials = (int)c.ls_trials;
+    o.last_branch = c.last_branch;
+    o.converged = c.converged;
+    o.obj = c.J;
+    o.mismatch = c.mis;
+    o.rel_grad_inf = c.rel_grad_inf;
+    o.grad_inf0 = c.g0inf;
+    o.rho_mem = c.rho_mem;
+    o.last_rho = c.last_rho;
+    k = c.k;
+    if (c.status != 0) {
+      rstarted = false;
+      if (c.status == kResErrLinesearch)
+        set_err(ctx, "Armijo line search failed after %d halvings (iteration %d)", ctx->opts.max_backtracks, c.k);
+      else
+        set_err(ctx, "non-finite objective or gradient (iteration %d)", c.k);
+      throw Fail{(ga_status)c.status};
+    }
+    rstarted = true;
+  }
+  void res_build() {
+    if (rexec) return;
+    cudaGraph_t top = nullptr;
+    ck(cudaGraphCreate(&top, 0), "graph create");
+    try {
+      add_resident(top);
+    } catch (...) {
+      cudaGraphDestroy(top);
+      throw;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&rexec, top, 0);
+    cudaGraphDestroy(top);
+    ck(e, "graph instantiate");
+  }
+  // Runs the solve's graph on st until k = kmax (or convergence when stop != 0). A fresh run starts from
+  // vin (device, vl values); otherwise it continues from the state of the last run.
+  void res_run(const T* vin, bool fresh, int kmax, int stop) {
+    res_build();
+    res_stage(vin, fresh, kmax, stop);
+    ck(cudaEventRecord(ev[0], st), "event");
+    ck(cudaGraphLaunch(rexec, st), "graph launch");
+    ck(cudaEventRecord(ev[1], st), "event");
+    res_complete();
+  }
+  void res_stage(const T* vin, bool fresh, int kmax, int stop) {
+    if (fresh) ck(cudaMemcpyAsync(VC, vin, sizeof(T) * vl, cudaMemcpyDeviceToDevice, st), "copy v");
+    res_prepare(fresh, kmax, stop);
+  }
+  // After the run's launch on st (bracketed by ev[0] and ev[1]): fetch the control block and finish.
+  void res_complete() {
+    res_fetch();
+    ck(cudaStreamSynchronize(st), "sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    res_finish(ms);
+  }
+
   void reset() {
     while (!win.empty()) {
       vfree.push_back(win.back().first);
@@ -702,6 +1019,7 @@ template <typename T> struct Engine : EngineBase {
     g0inf = 0.0;
     ctx->stats = ga_stats{};
     ctx->stats.rho_mem = 1.0;
+    rstarted = false;
   }
 
   T* take(std::vector<T*>& pool) {
@@ -734,7 +1052,7 @@ template <typename T> struct Engine : EngineBase {
   T* cur_g = nullptr;
 
   bool aa() const { return ctx->opts.method == GA_METHOD_GA_AA; }
-  T* current() const { return aa() ? cur_v : win.front().first; }
+  T* current() const { return resident ? VC : (aa() ? cur_v : win.front().first); }
 
   // Append (q, r) as the newest GA-AA window entry, dropping the oldest beyond w entries.
   void push_aa(T* q, T* r) {
@@ -977,6 +1295,37 @@ template <typename T> void stage_out(Engine<T>& e, void* p, const T* src, long l
 
 }  // namespace
 
+// One-launch batch graphs of the device-driven solve, by the exact list of contexts (dropped with any
+// of them).
+struct BatchGraph {
+  std::vector<ga_ctx*> key;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (stream) cudaStreamDestroy(stream);
+    if (done) cudaEventDestroy(done);
+    exec = nullptr;
+    stream = nullptr;
+    done = nullptr;
+  }
+};
+static std::mutex g_batch_mu;
+static std::deque<BatchGraph> g_batches;
+static void drop_batches_of(ga_ctx* c) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (auto it = g_batches.begin(); it != g_batches.end();) {
+    if (std::find(it->key.begin(), it->key.end(), c) != it->key.end()) {
+      if (it->stream) cudaStreamSynchronize(it->stream);
+      it->release();
+      it = g_batches.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 static thread_local std::string g_setup_err;
 
 namespace ga {
@@ -1020,7 +1369,8 @@ ga_status ga_setup(const ga_problem_desc* desc, const ga_solver_opts* opts, cons
   ok = ok && o.window >= 0 && o.window < kMaxWin && o.window + 2 <= kMaxDots && o.sigma >= 1 && o.tau >= 0 &&
        o.max_iter >= 1 && o.rel_tol >= 0.0 && o.armijo_c > 0.0 && o.max_backtracks >= 0 &&
        o.max_backtracks <= 200 && (o.variant == 1 || o.variant == 2) &&
-       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD || o.method == GA_METHOD_GA_AA) && (o.graphs == 0 || o.graphs == 1);
+       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD || o.method == GA_METHOD_GA_AA) &&
+       (o.graphs == 0 || o.graphs == 1 || (o.graphs == 2 && o.method != GA_METHOD_GA_AA));
   if (!ok) {
     g_setup_err = "invalid problem descriptor or solver options";
     return GA_ERR_ARG;
@@ -1056,6 +1406,7 @@ void ga_destroy(ga_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   else cudaDeviceSynchronize();
+  drop_batches_of(ctx);
   delete ctx->ef;
   delete ctx->ed;
   delete ctx;
@@ -1137,11 +1488,17 @@ ga_status ga_step(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
   if (!ctx || !v_inout || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) return GA_ERR_ARG;
   const auto t0 = std::chrono::steady_clock::now();
   ga_status s = dispatch(ctx, [&](auto& e) {
-    if (!e.started) {
-      auto* vin = stage_in(e, v_inout, e.vl, mem, e.io_a);
-      e.start(vin);
+    if (e.resident) {  // one iteration of the device-driven solve (a fresh start first if needed)
+      const bool fresh = !e.rstarted;
+      auto* vin = fresh ? stage_in(e, v_inout, e.vl, mem, e.io_a) : nullptr;
+      e.res_run(vin, fresh, fresh ? 1 : e.k + 1, 0);
+    } else {
+      if (!e.started) {
+        auto* vin = stage_in(e, v_inout, e.vl, mem, e.io_a);
+        e.start(vin);
+      }
+      e.step();
     }
-    e.step();
     stage_out(e, v_inout, e.current(), e.vl, mem);
   });
   ctx->stats.t_total_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1154,6 +1511,11 @@ ga_status ga_solve(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
   const auto t0 = std::chrono::steady_clock::now();
   ga_status s = dispatch(ctx, [&](auto& e) {
     auto* vin = stage_in(e, v_inout, e.vl, mem, e.io_a);
+    if (e.resident) {  // the whole solve is one graph launch
+      e.res_run(vin, true, ctx->opts.max_iter, 1);
+      stage_out(e, v_inout, e.current(), e.vl, mem);
+      return;
+    }
     e.start(vin);
     if (ctx->stats.rel_grad_inf > ctx->opts.rel_tol) {
       while (e.k < ctx->opts.max_iter) {
@@ -1171,10 +1533,99 @@ ga_status ga_solve(ga_ctx* ctx, void* v_inout, int mem, ga_stats* stats) {
   return s;
 }
 
+// The status of a batch: the first failure in problem order, else GA_ERR_NOT_CONVERGED if any problem
+// hit its iteration cap, else GA_OK.
+static ga_status batch_status(int count, ga_ctx* const* ctxs, const std::vector<ga_status>& st) {
+  ga_status worst = GA_OK;
+  for (int i = 0; i < count; ++i) {
+    if (st[i] == GA_ERR_NOT_CONVERGED) {
+      if (worst == GA_OK) worst = st[i];
+    } else if (st[i] != GA_OK) {
+      ga::set_global_error(("problem " + std::to_string(i) + ": " + ctxs[i]->err).c_str());
+      return st[i];
+    }
+  }
+  return worst;
+}
+
+// All contexts device-driven: every problem's whole solve is one chain of the same graph, launched
+// once; the graph is kept for the next call with the same contexts.
+static ga_status solve_batch_resident(int count, ga_ctx* const* ctxs, void* const* v, int mem, ga_stats* stats) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  std::vector<ga_status> st(count, GA_OK);
+  for (int i = 0; i < count; ++i) {
+    ga_ctx* c = ctxs[i];
+    const ga_status s = dispatch(c, [&](auto& e) {
+      auto* vin = stage_in(e, v[i], e.vl, mem, e.io_a);
+      e.res_stage(vin, true, c->opts.max_iter, 1);
+      e.ck(cudaEventRecord(e.ev[0], e.st), "event");
+    });
+    if (s != GA_OK) {
+      ga::set_global_error(("problem " + std::to_string(i) + ": " + c->err).c_str());
+      return s;
+    }
+  }
+  const std::vector<ga_ctx*> key(ctxs, ctxs + count);
+  BatchGraph* bg = nullptr;
+  for (auto& b : g_batches)
+    if (b.key == key) bg = &b;
+  if (!bg) {
+    BatchGraph nb;
+    nb.key = key;
+    cudaGraph_t top = nullptr;
+    cudaError_t e = cudaGraphCreate(&top, 0);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+      const ga_status s = dispatch(ctxs[i], [&](auto& en) { en.add_resident(top); });
+      if (s != GA_OK) {
+        cudaGraphDestroy(top);
+        ga::set_global_error(("problem " + std::to_string(i) + ": " + ctxs[i]->err).c_str());
+        return s;
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&nb.exec, top, 0);
+    if (top) cudaGraphDestroy(top);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&nb.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&nb.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      nb.release();
+      ga::set_global_error((std::string("batch graph: ") + cudaGetErrorString(e)).c_str());
+      return GA_ERR_CUDA;
+    }
+    g_batches.push_back(nb);
+    bg = &g_batches.back();
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < count && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(bg->stream, ctxs[i]->ef ? ctxs[i]->ef->ev[0] : ctxs[i]->ed->ev[0], 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(bg->exec, bg->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(bg->done, bg->stream);
+  if (e != cudaSuccess) {
+    ga::set_global_error((std::string("batch launch: ") + cudaGetErrorString(e)).c_str());
+    return GA_ERR_CUDA;
+  }
+  for (int i = 0; i < count; ++i) {
+    ga_ctx* c = ctxs[i];
+    const auto t0 = std::chrono::steady_clock::now();
+    st[i] = dispatch(c, [&](auto& en) {
+      en.ck(cudaStreamWaitEvent(en.st, bg->done, 0), "wait");
+      en.ck(cudaEventRecord(en.ev[1], en.st), "event");
+      en.res_complete();
+      stage_out(en, v[i], en.current(), en.vl, mem);
+    });
+    c->stats.t_total_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (st[i] == GA_OK && !c->stats.converged) st[i] = GA_ERR_NOT_CONVERGED;
+    if (stats) stats[i] = c->stats;
+  }
+  return batch_status(count, ctxs, st);
+}
+
 ga_status ga_solve_batch(int count, ga_ctx* const* ctxs, void* const* v, int mem, ga_stats* stats) {
   if (count < 0 || (count > 0 && (!ctxs || !v))) return GA_ERR_ARG;
   for (int i = 0; i < count; ++i)
     if (!ctxs[i] || !v[i]) return GA_ERR_ARG;
+  bool all_resident = count > 0;
+  for (int i = 0; i < count; ++i) all_resident = all_resident && ctxs[i]->opts.graphs == 2;
+  if (all_resident) return solve_batch_resident(count, ctxs, v, mem, stats);
   // Each problem is solved by its own host worker on its own context stream, so the kernels of
   // different problems overlap on the GPU while any one of them waits for a line-search decision.
   int dev = 0;
@@ -1192,16 +1643,7 @@ ga_status ga_solve_batch(int count, ga_ctx* const* ctxs, void* const* v, int mem
   for (int t = 1; t < nworkers; ++t) pool.emplace_back(worker);
   worker();
   for (auto& th : pool) th.join();
-  ga_status worst = GA_OK;
-  for (int i = 0; i < count; ++i) {
-    if (st[i] == GA_ERR_NOT_CONVERGED) {
-      if (worst == GA_OK) worst = st[i];
-    } else if (st[i] != GA_OK) {
-      ga::set_global_error(("problem " + std::to_string(i) + ": " + ctxs[i]->err).c_str());
-      return st[i];
-    }
-  }
-  return worst;
+  return batch_status(count, ctxs, st);
 }
 
 // ---- operator-level entry points (ga_ops.h) --------------------------------------------------------
@@ -1268,6 +1710,37 @@ ga_status ga_op_deriv(ga_ctx* ctx, const void* f, int axis, void* df) {
     e.deriv(e.g.axis_of(axis), static_cast<const T*>(f), nullptr, static_cast<T*>(df), 1.0, false);
     e.ck(cudaStreamSynchronize(e.st), "sync");
   });
+}
+
+ga_status ga_op_get_tiles(const ga_ctx* ctx, int* pencils) {
+  if (!ctx || !pencils) return GA_ERR_ARG;
+  const int dim = ctx->desc.dim;
+  for (int c = 0; c < dim; ++c) {
+    const int a = 3 - dim + c;
+    const int L = ctx->desc.n[c];
+    const int p = ctx->ef ? ctx->ef->ft.deriv_pencils[a] : ctx->ed->ft.deriv_pencils[a];
+    pencils[c] = p > 0 ? p : (ctx->ef ? ga::deriv_default_pencils<float>(L) : ga::deriv_default_pencils<double>(L));
+  }
+  return GA_OK;
+}
+
+ga_status ga_op_set_tiles(ga_ctx* ctx, const int* pencils) {
+  if (!ctx || !pencils) return GA_ERR_ARG;
+  const int dim = ctx->desc.dim;
+  for (int c = 0; c < dim; ++c) {
+    const int L = ctx->desc.n[c];
+    const bool fits = ctx->ef ? ga::deriv_pencils_fit<float>(L, pencils[c]) : ga::deriv_pencils_fit<double>(L, pencils[c]);
+    if (pencils[c] < 0 || (pencils[c] > 0 && !fits)) {
+      set_err(ctx, "ga_op_set_tiles: %d pencils per CTA along axis %d do not fit", pencils[c], c);
+      return GA_ERR_ARG;
+    }
+  }
+  for (int c = 0; c < dim; ++c) {
+    const int a = 3 - dim + c;
+    if (ctx->ef) ctx->ef->ft.deriv_pencils[a] = pencils[c];
+    else ctx->ed->ft.deriv_pencils[a] = pencils[c];
+  }
+  return GA_OK;
 }
 
 ga_status ga_op_div(ga_ctx* ctx, const void* v, void* mu) {

@@ -77,9 +77,10 @@ __device__ __forceinline__ double block_max(double x) {
   return r;
 }
 
+// Per-CTA partial sums of <a, b_k> for k < count (count <= NB).
 template <typename T, int NB>
-__global__ void __launch_bounds__(kThreads)
-k_dots(const T* __restrict__ a, PtrList<T> b, int count, long long len, double* __restrict__ partial) {
+__device__ __forceinline__ void dots_body(const T* __restrict__ a, const T* const* b, int count, long long len,
+                                          double* __restrict__ partial) {
   using Acc = typename AccOf<T>::type;
   Acc acc[NB];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
@@ -87,7 +88,7 @@ k_dots(const T* __restrict__ a, PtrList<T> b, int count, long long len, double* 
     const T av = a[i];
 #pragma unroll
     for (int k = 0; k < NB; ++k)
-      if (k < count) acc[k].add_prod(av, b.p[k][i]);
+      if (k < count) acc[k].add_prod(av, b[k][i]);
   }
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
@@ -96,6 +97,39 @@ k_dots(const T* __restrict__ a, PtrList<T> b, int count, long long len, double* 
       if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = s;
     }
   }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads)
+k_dots(const T* __restrict__ a, PtrList<T> b, int count, long long len, double* __restrict__ partial) {
+  dots_body<T, NB>(a, b.p, count, len, partial);
+}
+
+// ---- window ring of the device-driven solve ---------------------------------------------------
+__device__ __forceinline__ int ring_slot(int head, int i, int W1) { return (((head - i) % W1) + W1) % W1; }
+__device__ __forceinline__ int ring_head(const ResCtl* c, int W1) { return ring_slot(c->head, 0, W1); }
+// entries of the ring that take part: all m, or the min(m, W1 - 1) a push keeps
+__device__ __forceinline__ int ring_count(const ResCtl* c, int W1, int keep) {
+  const int m = min(max(c->m, 0), W1);
+  return keep ? min(m, W1 - 1) : m;
+}
+
+// Chunk `chunk` (16 products) of out = [<a, first>, <a, ring entry 0>, ...].
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_dots_ring(const T* __restrict__ a, const T* __restrict__ first, const T* __restrict__ ring, long long stride,
+            const ResCtl* __restrict__ c, int W1, int keep, int chunk, long long len, double* __restrict__ partial) {
+  const int count = 1 + ring_count(c, W1, keep), base = 16 * chunk;
+  const int cnt = min(16, count - base);
+  if (cnt <= 0) return;
+  const int head = ring_head(c, W1);
+  const T* b[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int e = base + k;
+    b[k] = (k >= cnt) ? nullptr : (e == 0 ? first : ring + (long long)ring_slot(head, e - 1, W1) * stride);
+  }
+  dots_body<T, 16>(a, b, cnt, len, partial + (long long)base * gridDim.x);
 }
 
 template <typename T>
@@ -132,8 +166,8 @@ k_mismatch(const T* __restrict__ mT, const T* __restrict__ m1, T* __restrict__ l
 
 // out[k] = sum_b partial[k * nblocks + b], k < count: one warp per output, each lane sums a fixed
 // strided subset in FP64 (Neumaier), then a fixed shuffle tree; deterministic.
-__global__ void k_sum_partials(const double* __restrict__ partial, int count, int nblocks,
-                               double* __restrict__ out) {
+__device__ __forceinline__ void sum_partials_body(const double* __restrict__ partial, int count, int nblocks,
+                                                  double* __restrict__ out) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= count) return;
   double s = 0.0, c = 0.0;
@@ -146,6 +180,16 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int count, in
   s += c;
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if (lane == 0) out[k] = s;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int count, int nblocks,
+                               double* __restrict__ out) {
+  sum_partials_body(partial, count, nblocks, out);
+}
+
+__global__ void k_sum_partials_ring(const double* __restrict__ partial, const ResCtl* __restrict__ c, int W1,
+                                    int keep, int nblocks, double* __restrict__ out) {
+  sum_partials_body(partial, 1 + ring_count(c, W1, keep), nblocks, out);
 }
 
 __global__ void k_max_partials(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
@@ -171,8 +215,18 @@ k_axpy(T* __restrict__ y, const T* __restrict__ x, const T* __restrict__ s, T a,
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_combine(T* __restrict__ out, const T* __restrict__ q, PtrList<T> v, const double* __restrict__ beta,
-          int m, int accumulate, long long len) {
+k_axpy_dev(T* __restrict__ y, const T* __restrict__ x, const T* __restrict__ s, const double* __restrict__ a,
+           long long len) {
+  const T av = (T)*a;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] + av * s[i];
+}
+
+// out (+)= q + sum_{k < m} beta_k (q - v_k) for one chunk of at most 16 vectors
+template <typename T>
+__device__ __forceinline__ void combine_body(T* __restrict__ out, const T* __restrict__ q, const T* const* v,
+                                             const double* __restrict__ beta, int m, int accumulate, long long len) {
   T bt[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) bt[k] = k < m ? (T)beta[k] : T(0);
@@ -182,9 +236,41 @@ k_combine(T* __restrict__ out, const T* __restrict__ q, PtrList<T> v, const doub
     T acc = accumulate ? out[i] : qi;
 #pragma unroll
     for (int k = 0; k < 16; ++k)
-      if (k < m) acc += bt[k] * (qi - v.p[k][i]);
+      if (k < m) acc += bt[k] * (qi - v[k][i]);
     out[i] = acc;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_combine(T* __restrict__ out, const T* __restrict__ q, PtrList<T> v, const double* __restrict__ beta,
+          int m, int accumulate, long long len) {
+  combine_body<T>(out, q, v.p, beta, m, accumulate, len);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_combine_ring(T* __restrict__ out, const T* __restrict__ q, const T* __restrict__ ring, long long stride,
+               const ResCtl* __restrict__ c, int W1, const double* __restrict__ beta, int chunk, long long len) {
+  const int m = ring_count(c, W1, 0), base = 16 * chunk;
+  const int cnt = min(16, m - base);
+  if (cnt <= 0 && chunk > 0) return;
+  const int head = ring_head(c, W1);
+  const T* v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = k < cnt ? ring + (long long)ring_slot(head, base + k, W1) * stride : nullptr;
+  combine_body<T>(out, q, v, beta + base, cnt, chunk > 0 ? 1 : 0, len);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_ring_store(T* __restrict__ ring, long long stride, const ResCtl* __restrict__ c, int W1, const T* __restrict__ src,
+             long long len) {
+  if (c->status != 0) return;
+  T* dst = ring + (long long)ring_slot(ring_head(c, W1) + 1, 0, W1) * stride;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
 }
 
 // Cyclic Jacobi eigen-solve of the m x m normal equations (m <= kMaxWin) by one warp, with G, U and
@@ -193,7 +279,12 @@ k_combine(T* __restrict__ out, const T* __restrict__ q, PtrList<T> v, const doub
 // operations in the same order as in a one-thread loop, and the scalar sums are taken by lane 0, so
 // the result does not depend on the warp width.
 __global__ void __launch_bounds__(32) k_lsq(int m, const double* __restrict__ dots, const double* __restrict__ M,
-                                            int ldm, double* __restrict__ beta, double* __restrict__ info) {
+                                            int ldm, double* __restrict__ beta, double* __restrict__ info,
+                                            const ResCtl* __restrict__ ctl) {
+  if (ctl) {  // device-driven solve: m is the window size on the device
+    if (ctl->status != 0) return;
+    m = min(max(ctl->m, 1), min(ldm, kMaxWin));
+  }
   extern __shared__ double sh[];
   double* G = sh;              // m * m
   double* U = sh + m * m;      // m * m
@@ -285,8 +376,13 @@ __global__ void __launch_bounds__(32) k_lsq(int m, const double* __restrict__ do
   }
 }
 
-__global__ void k_gram_push(double* __restrict__ M, int ldm, int mkeep, const double* __restrict__ row) {
+__global__ void k_gram_push(double* __restrict__ M, int ldm, int mkeep, const double* __restrict__ row,
+                            const ResCtl* __restrict__ ctl) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (ctl) {  // device-driven solve: keep min(m, W1 - 1) entries
+    if (ctl->status != 0) return;
+    mkeep = min(max(ctl->m, 0), ldm - 1);
+  }
   // shift the kept block down-right by one, in place from the bottom-right corner
   for (int i = mkeep - 1; i >= 0; --i)
     for (int j = mkeep - 1; j >= 0; --j) M[(i + 1) * ldm + (j + 1)] = M[i * ldm + j];
@@ -390,9 +486,8 @@ cudaError_t launch_combine(T* out, const T* q, const T* const* v, const double* 
   return cudaSuccess;
 }
 
-cudaError_t launch_lsq(int m, const double* dots, const double* M, int ldm, double* beta, double* info,
-                       cudaStream_t st) {
-  if (m < 1 || m > kMaxWin) return cudaErrorInvalidValue;
+namespace {
+cudaError_t lsq_smem_limit() {
   constexpr size_t kMaxSmem = sizeof(double) * (2 * kMaxWin * kMaxWin + kMaxWin);
   static std::atomic<bool> attr{false};
   if (!attr.load()) {  // one process-wide setting, the largest size any call needs
@@ -400,14 +495,85 @@ cudaError_t launch_lsq(int m, const double* dots, const double* M, int ldm, doub
     if (e != cudaSuccess) return e;
     attr.store(true);
   }
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_lsq(int m, const double* dots, const double* M, int ldm, double* beta, double* info,
+                       cudaStream_t st) {
+  if (m < 1 || m > kMaxWin) return cudaErrorInvalidValue;
+  cudaError_t e = lsq_smem_limit();
+  if (e != cudaSuccess) return e;
   note_launches(1);
-  k_lsq<<<1, 32, sizeof(double) * (2 * m * m + m), st>>>(m, dots, M, ldm, beta, info);
+  k_lsq<<<1, 32, sizeof(double) * (2 * m * m + m), st>>>(m, dots, M, ldm, beta, info, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_push(double* M, int ldm, int mkeep, const double* row, cudaStream_t st) {
   note_launches(1);
-  k_gram_push<<<1, 32, 0, st>>>(M, ldm, mkeep, row);
+  k_gram_push<<<1, 32, 0, st>>>(M, ldm, mkeep, row, nullptr);
+  return cudaGetLastError();
+}
+
+// ---- ring variants of the device-driven solve ---------------------------------------------------
+template <typename T>
+cudaError_t launch_axpy_dev(T* y, const T* x, const T* s, const double* a, long long len, cudaStream_t st) {
+  note_launches(1);
+  k_axpy_dev<T><<<grid_for(len), kThreads, 0, st>>>(y, x, s, a, len);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dots_ring(const T* a, const T* first, const T* ring, long long stride, const ResCtl* c, int W1,
+                             int keep, long long len, double* partial, double* out, cudaStream_t st) {
+  if (W1 < 1 || 1 + W1 > kMaxDots) return cudaErrorInvalidValue;
+  for (int chunk = 0; 16 * chunk < 1 + W1; ++chunk) {
+    note_launches(1);
+    k_dots_ring<T><<<kRedBlocks, kThreads, 0, st>>>(a, first, ring, stride, c, W1, keep, chunk, len, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  note_launches(1);
+  const int most = 1 + W1;
+  k_sum_partials_ring<<<(most + 31) / 32, 32 * (most < 32 ? most : 32), 0, st>>>(partial, c, W1, keep, kRedBlocks,
+                                                                               out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_combine_ring(T* out, const T* q, const T* ring, long long stride, const ResCtl* c, int W1,
+                                const double* beta, long long len, cudaStream_t st) {
+  if (W1 < 1 || W1 > kMaxWin) return cudaErrorInvalidValue;
+  for (int chunk = 0; 16 * chunk < W1; ++chunk) {
+    note_launches(1);
+    k_combine_ring<T><<<grid_for(len), kThreads, 0, st>>>(out, q, ring, stride, c, W1, beta, chunk, len);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_ring_store(T* ring, long long stride, const ResCtl* c, int W1, const T* src, long long len,
+                              cudaStream_t st) {
+  note_launches(1);
+  k_ring_store<T><<<grid_for(len), kThreads, 0, st>>>(ring, stride, c, W1, src, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lsq_ring(const ResCtl* c, int W1, const double* dots, const double* M, double* beta, double* info,
+                            cudaStream_t st) {
+  if (W1 < 1 || W1 > kMaxWin) return cudaErrorInvalidValue;
+  cudaError_t e = lsq_smem_limit();
+  if (e != cudaSuccess) return e;
+  note_launches(1);
+  k_lsq<<<1, 32, sizeof(double) * (2 * W1 * W1 + W1), st>>>(W1, dots, M, W1, beta, info, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_push_ring(double* M, int W1, const ResCtl* c, const double* row, cudaStream_t st) {
+  note_launches(1);
+  k_gram_push<<<1, 32, 0, st>>>(M, W1, 0, row, c);
   return cudaGetLastError();
 }
 
@@ -420,7 +586,14 @@ cudaError_t launch_gram_push(double* M, int ldm, int mkeep, const double* row, c
   template cudaError_t launch_axpy<T>(T*, const T*, const T*, double, long long, cudaStream_t);       \
   template cudaError_t launch_fill<T>(T*, double, long long, cudaStream_t);                          \
   template cudaError_t launch_combine<T>(T*, const T*, const T* const*, const double*, int, long long, \
-                                         cudaStream_t);
+                                         cudaStream_t);                                              \
+  template cudaError_t launch_axpy_dev<T>(T*, const T*, const T*, const double*, long long, cudaStream_t); \
+  template cudaError_t launch_dots_ring<T>(const T*, const T*, const T*, long long, const ResCtl*, int, int, \
+                                           long long, double*, double*, cudaStream_t);                \
+  template cudaError_t launch_combine_ring<T>(T*, const T*, const T*, long long, const ResCtl*, int,     \
+                                              const double*, long long, cudaStream_t);                \
+  template cudaError_t launch_ring_store<T>(T*, long long, const ResCtl*, int, const T*, long long,     \
+                                            cudaStream_t);
 GA_INST(float)
 GA_INST(double)
 #undef GA_INST

@@ -74,7 +74,8 @@ def test_setup_rejects_bad_descriptors(libga, bad):
 
 
 @pytest.mark.parametrize("bad", [dict(window=63), dict(sigma=0), dict(tau=-1), dict(max_iter=0),
-                                 dict(variant=3), dict(armijo_c=0.0), dict(method=5)])
+                                 dict(variant=3), dict(armijo_c=0.0), dict(method=5), dict(graphs=3),
+                                 dict(graphs=2, method=2)])
 def test_setup_rejects_bad_options(libga, bad):
     d, o = _desc(libga)
     for k, v in bad.items():
