@@ -43,7 +43,7 @@ WORKLOAD_NAME = ("cont3d256: 256^3 continuity (mass-preserving), nt=16, H1 alpha
 CPU_SAMPLE_N = 48  # oracle sample grid (same recipe), scaled to 256^3 by voxel count
 
 # kernel classes timed with events inside the library (ga_prof_start)
-PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ = 0, 1, 2, 3
+PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ, PROF_DERIV_PAIR = 0, 1, 2, 3, 4
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sl_tile2<1> launch from an ncu
 # capture of this benchmark at 192^3 (143.4 MB read + 16.7 MB written, mean of 3 launches), scaled to
@@ -452,7 +452,9 @@ def main():
     algo = {PROF_SL_FWD: ("sl_forward continuity step: read pi_j, mu, 3 displacement fields, write pi_{j+1}", 24),
             PROF_SL_ADJ: ("sl_adjoint continuity step: read lambda_{j+1}, 3 displacement fields, write lambda_j", 20),
             PROF_DERIV: ("fused FFT-derivative pass: read f, read multiplier, read+write accumulator", 16),
-            PROF_FFT: ("3D real FFT (3 passes)", 24)}[args.prof_class]
+            PROF_FFT: ("3D real FFT (3 passes)", 24),
+            PROF_DERIV_PAIR: ("body-force FFT-derivative pass over two time steps: read f, f2, multiplier, "
+                              "multiplier2, read+write accumulator", 24)}[args.prof_class]
     hbm, peak_kind = peaks()
     per_launch_ms = prof_ms / max(prof_n, 1)
     bytes_per_launch = algo[1] * nv

@@ -96,8 +96,8 @@ ga_status ga_transport_vjp_exact(ga_ctx* ctx, const void* v, const void* gamma, 
 
 /* Device-time accounting of one kernel class over a region of calls, with CUDA events recorded
  * on the context stream around every launch of that class: 0 = semi-Lagrangian state steps,
- * 1 = fused FFT-derivative passes, 2 = 3D FFT transforms (all passes of one transform),
- * 3 = semi-Lagrangian adjoint steps. ga_prof_stop returns the summed event time (ms) and the
+ * 1 = fused FFT-derivative passes of one field, 2 = 3D FFT transforms (all passes of one transform),
+ * 3 = semi-Lagrangian adjoint steps, 4 = body-force derivative passes over two time steps. ga_prof_stop returns the summed event time (ms) and the
  * number of timed launches since ga_prof_start, and ends the accounting. */
 ga_status ga_prof_start(ga_ctx* ctx, int kernel_class);
 ga_status ga_prof_stop(ga_ctx* ctx, double* total_ms, long long* launches);

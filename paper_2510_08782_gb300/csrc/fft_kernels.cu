@@ -29,6 +29,27 @@ namespace {
 constexpr int PS = 4;
 __device__ __forceinline__ int pd(int i) { return fpad<PS>(i); }
 
+// (q, r) = (i / d, i % d) along a block-strided loop i = threadIdx.x, threadIdx.x + blockDim.x, ...:
+// one division per thread, then constant steps (a runtime divisor costs a long instruction sequence
+// per division).
+struct StridedQR {
+  int q, r, d, dq, dr;
+  __device__ __forceinline__ StridedQR(int i, int d_) : d(d_) {
+    q = i / d;
+    r = i - q * d;
+    dq = (int)blockDim.x / d;
+    dr = (int)blockDim.x - dq * d;
+  }
+  __device__ __forceinline__ void next() {
+    q += dq;
+    r += dr;
+    if (r >= d) {
+      r -= d;
+      ++q;
+    }
+  }
+};
+
 // Compile-time stage sequence for a fixed length N (radices from ct_next_radix, at most MAXR).
 template <typename T, int N, int Ns, int MAXR> struct CtStages {
   __device__ __forceinline__ static cx<T>* run(cx<T>* a, cx<T>* b, int B, int ld, const cx<T>* tw) {
@@ -93,9 +114,10 @@ template <typename T, int N, int R, int Ns, bool PFAST, typename Load, typename 
 __device__ __forceinline__ void fused_stage(Load& load, Fin& fin, const cx<T>* in, cx<T>* out, int B, int ld,
                                             const cx<T>* tw) {
   constexpr int M = N / R;
-  for (int t = threadIdx.x; t < B * M; t += blockDim.x) {
-    const bool pf = PFAST && Ns == 1;
-    const int p = pf ? t % B : t / M, j = pf ? t / B : t - (t / M) * M;
+  constexpr bool pf = PFAST && Ns == 1;
+  StridedQR qr(threadIdx.x, pf ? B : 1);  // pencil-fastest order: t = j * B + p
+  for (int t = threadIdx.x; t < B * M; t += blockDim.x, qr.next()) {
+    const int p = pf ? qr.r : t / M, j = pf ? qr.q : t - (t / M) * M;
     const int k = j % Ns;
     cx<T> v[R];
     if constexpr (Ns == 1) {
@@ -193,15 +215,13 @@ __device__ __forceinline__ void stage_rows(T* dst, const T* src, int L, long lon
   constexpr int per = 16 / sizeof(T);
   if (vec) {  // W % per == 0, valid == W, 16-byte aligned rows
     const int cpr = W / per;
-    for (int c = threadIdx.x; c < L * cpr; c += blockDim.x) {
-      const int j = c / cpr, k = c - j * cpr;
-      cpa16(dst + j * W + k * per, src + j * S + k * per);
-    }
+    StridedQR qr(threadIdx.x, cpr);
+    for (int c = threadIdx.x; c < L * cpr; c += blockDim.x, qr.next())
+      cpa16(dst + qr.q * W + qr.r * per, src + qr.q * S + qr.r * per);
   } else {
-    for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
-      const int j = e / W, x = e - j * W;
-      if (x < valid) cpa_elem<T>(dst + e, src + j * S + x);
-    }
+    StridedQR qr(threadIdx.x, W);
+    for (int e = threadIdx.x; e < L * W; e += blockDim.x, qr.next())
+      if (qr.r < valid) cpa_elem<T>(dst + e, src + qr.q * S + qr.r);
   }
 }
 
@@ -226,34 +246,73 @@ template <typename T> struct DerivSmem {
   }
 };
 
+// Operands of a derivative pass: out (+)= coef * mult * d f (one time step), or with PAIR
+// out (+)= coef * mult * d f + coef2 * mult2 * d f2 (two time steps of the body force in one pass:
+// f and f2 are the real and imaginary parts of one complex pencil, as two columns are otherwise).
+// A null multiplier means 1. The sum is formed as two successive single passes would form it.
+template <typename T> struct DerivIO {
+  const T* f;
+  const T* mult;
+  const T* f2;
+  const T* mult2;
+  T* out;
+  T coef, coef2;
+  int accumulate;
+};
+
+template <typename T, bool PAIR>
+__device__ __forceinline__ T deriv_out(const DerivIO<T>& io, const DerivSmem<T>& sm, int e, int plane, cx<T> z, T inv,
+                                       bool odd) {
+  if constexpr (PAIR) {
+    T v1 = io.coef * (z.x * inv);
+    if (io.mult) v1 *= sm.mult[e];
+    if (io.accumulate) v1 += sm.acc[e];
+    T v2 = io.coef2 * (-z.y * inv);
+    if (io.mult2) v2 *= sm.mult[plane + e];
+    return v2 + v1;
+  } else {
+    T val = io.coef * (odd ? -z.y * inv : z.x * inv);
+    if (io.mult) val *= sm.mult[e];
+    if (io.accumulate) val += sm.acc[e];
+    return val;
+  }
+}
+
 // ---- derivative along the contiguous axis (rows) --------------------------------------------
 // Rows row0 .. row0 + 2B - 1 are one contiguous block: staged raw, then paired (2p, 2p+1) into
-// complex pencils.
-template <typename T, int NC>
+// complex pencils. PAIR: rows row0 .. row0 + B - 1 of f and of f2, paired (f row p, f2 row p).
+template <typename T, int NC, bool PAIR>
 __global__ void __launch_bounds__(kThreads)
-k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
-             int accumulate, long long rows, int Lr, int B, int ld, FftPlan plan,
-             const cx<T>* __restrict__ twg, int vec) {
+k_deriv_rows(DerivIO<T> io, long long rows, int Lr, int B, int ld, FftPlan plan, const cx<T>* __restrict__ twg,
+             int vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = NC > 0 ? NC : Lr;
   DerivSmem<T> sm(smem_raw, L, B, ld);
-  const long long row0 = (long long)blockIdx.x * 2 * B;
-  const int nrows = (int)((rows - row0) < 2 * B ? (rows - row0) : 2 * B);
-  const bool full = nrows == 2 * B && vec;
-  stage_contig<T>(sm.raw, f + row0 * L, nrows * L, full);
+  constexpr int RPC = PAIR ? 1 : 2;  // rows of one field per complex pencil
+  const long long row0 = (long long)blockIdx.x * RPC * B;
+  const int nrows = (int)((rows - row0) < RPC * B ? (rows - row0) : RPC * B);
+  const bool full = nrows == RPC * B && vec;
+  const int plane = B * L;  // PAIR: offset of the second field's block in raw and mult
+  stage_contig<T>(sm.raw, io.f + row0 * L, nrows * L, full);
+  if (PAIR) stage_contig<T>(sm.raw + plane, io.f2 + row0 * L, nrows * L, full);
   cpa_commit();
-  if (mult) stage_contig<T>(sm.mult, mult + row0 * L, nrows * L, full);
-  if (accumulate) stage_contig<T>(sm.acc, out + row0 * L, nrows * L, full);
+  if (io.mult) stage_contig<T>(sm.mult, io.mult + row0 * L, nrows * L, full);
+  if (PAIR && io.mult2) stage_contig<T>(sm.mult + plane, io.mult2 + row0 * L, nrows * L, full);
+  if (io.accumulate) stage_contig<T>(sm.acc, io.out + row0 * L, nrows * L, full);
   cpa_commit();
   load_tw<T>(sm.tw, twg, L);
   cpa_wait<1>();
   __syncthreads();
-  cx<T>* r;
-  if constexpr (NC > 0) {  // rows 2p, 2p+1 read straight from the staged block; i k~ applied on the way out
-    const T* raw = sm.raw;
-    auto load = [&](int p, int i) {
+  const T* raw = sm.raw;
+  // element i of complex pencil p
+  auto load = [&](int p, int i) {
+    if constexpr (PAIR)
+      return (p < nrows) ? mk<T>(raw[p * L + i], raw[plane + p * L + i]) : mk<T>(T(0), T(0));
+    else
       return mk<T>((2 * p < nrows) ? raw[(2 * p) * L + i] : T(0), (2 * p + 1 < nrows) ? raw[(2 * p + 1) * L + i] : T(0));
-    };
+  };
+  cx<T>* r;
+  if constexpr (NC > 0) {  // read straight from the staged block; i k~ applied on the way out
     auto fin = [&](int k, cx<T> z) {
       const T kt = ktilde<T>(k, L);
       return mk<T>(-kt * z.y, -kt * z.x);
@@ -262,9 +321,7 @@ k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
   } else {
     for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
       const int p = idx / L, j = idx - p * L;
-      const T va = (2 * p < nrows) ? sm.raw[(2 * p) * L + j] : T(0);
-      const T vb = (2 * p + 1 < nrows) ? sm.raw[(2 * p + 1) * L + j] : T(0);
-      sm.a[p * ld + pd(j)] = mk<T>(va, vb);
+      sm.a[p * ld + pd(j)] = load(p, j);
     }
     __syncthreads();
     r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
@@ -277,54 +334,53 @@ k_deriv_rows(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
   const T inv = T(1) / T(L);
   for (int idx = threadIdx.x; idx < nrows * L; idx += blockDim.x) {
     const int rr = idx / L, j = idx - rr * L;
-    const cx<T> z = r2[(rr >> 1) * ld + pd(j)];
-    T val = coef * ((rr & 1) ? -z.y * inv : z.x * inv);
-    if (mult) val *= sm.mult[idx];
-    if (accumulate) val += sm.acc[idx];
-    out[row0 * L + idx] = val;
+    const cx<T> z = r2[(PAIR ? rr : (rr >> 1)) * ld + pd(j)];
+    io.out[row0 * L + idx] = deriv_out<T, PAIR>(io, sm, idx, plane, z, inv, (rr & 1) != 0);
   }
 }
 
-// ---- derivative along a strided axis (tiles of 2B adjacent columns) ---------------------------
-template <typename T, int NC>
+// ---- derivative along a strided axis (tiles of adjacent columns) -------------------------------
+// A tile holds W = 2B columns (PAIR: B columns of f and the same B columns of f2).
+template <typename T, int NC, bool PAIR>
 __global__ void __launch_bounds__(kThreads)
-k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict__ out, T coef,
-             int accumulate, int Lr, long long S, long long outer_stride, int nx, int B, int ld,
-             FftPlan plan, const cx<T>* __restrict__ twg, int vec) {
+k_deriv_cols(DerivIO<T> io, int Lr, long long S, long long outer_stride, int nx, int B, int ld, FftPlan plan,
+             const cx<T>* __restrict__ twg, int vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = NC > 0 ? NC : Lr;
   DerivSmem<T> sm(smem_raw, L, B, ld);
-  const int W = 2 * B;
+  const int W = PAIR ? B : 2 * B;
   const int x0 = blockIdx.x * W;
   const long long base = (long long)blockIdx.y * outer_stride + x0;
   const int valid = (nx - x0) < W ? (nx - x0) : W;
   const bool v16 = vec && valid == W;
-  stage_rows<T>(sm.raw, f + base, L, S, W, valid, v16);
+  const int plane = W * L;
+  stage_rows<T>(sm.raw, io.f + base, L, S, W, valid, v16);
+  if (PAIR) stage_rows<T>(sm.raw + plane, io.f2 + base, L, S, W, valid, v16);
   cpa_commit();
-  if (mult) stage_rows<T>(sm.mult, mult + base, L, S, W, valid, v16);
-  if (accumulate) stage_rows<T>(sm.acc, out + base, L, S, W, valid, v16);
+  if (io.mult) stage_rows<T>(sm.mult, io.mult + base, L, S, W, valid, v16);
+  if (PAIR && io.mult2) stage_rows<T>(sm.mult + plane, io.mult2 + base, L, S, W, valid, v16);
+  if (io.accumulate) stage_rows<T>(sm.acc, io.out + base, L, S, W, valid, v16);
   cpa_commit();
   load_tw<T>(sm.tw, twg, L);
   cpa_wait<1>();
   __syncthreads();
-  cx<T>* r;
-  if constexpr (NC > 0) {  // columns 2p, 2p+1 read straight from the staged tile; i k~ applied on the way out
-    const T* raw = sm.raw;
-    auto load = [&](int p, int i) {
+  const T* raw = sm.raw;
+  auto load = [&](int p, int i) {
+    if constexpr (PAIR)
+      return (p < valid) ? mk<T>(raw[i * W + p], raw[plane + i * W + p]) : mk<T>(T(0), T(0));
+    else
       return mk<T>((2 * p < valid) ? raw[i * W + 2 * p] : T(0), (2 * p + 1 < valid) ? raw[i * W + 2 * p + 1] : T(0));
-    };
+  };
+  cx<T>* r;
+  if constexpr (NC > 0) {  // read straight from the staged tile; i k~ applied on the way out
     auto fin = [&](int k, cx<T> z) {
       const T kt = ktilde<T>(k, L);
       return mk<T>(-kt * z.y, -kt * z.x);
     };
     r = FusedForward<T, NC, 1, 8, true>::run(load, fin, sm.b, sm.a, B, ld, sm.tw);  // sm.b holds the raw tile
   } else {
-    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-      const int j = idx / B, p = idx - j * B;
-      const T va = (2 * p < valid) ? sm.raw[j * W + 2 * p] : T(0);
-      const T vb = (2 * p + 1 < valid) ? sm.raw[j * W + 2 * p + 1] : T(0);
-      sm.a[p * ld + pd(j)] = mk<T>(va, vb);
-    }
+    StridedQR qr(threadIdx.x, B);
+    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x, qr.next()) sm.a[qr.r * ld + pd(qr.q)] = load(qr.r, qr.q);
     __syncthreads();
     r = run_fft<T, NC, 8>(sm.a, sm.b, L, B, ld, plan, sm.tw);
     mult_ik_conj<T>(r, B, L, ld);
@@ -334,14 +390,12 @@ k_deriv_cols(const T* __restrict__ f, const T* __restrict__ mult, T* __restrict_
   cpa_wait<0>();
   __syncthreads();
   const T inv = T(1) / T(L);
-  for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x) {
-    const int j = idx / W, xx = idx - j * W;
+  StridedQR qr(threadIdx.x, W);
+  for (int idx = threadIdx.x; idx < W * L; idx += blockDim.x, qr.next()) {
+    const int j = qr.q, xx = qr.r;
     if (xx >= valid) continue;
-    const cx<T> z = r2[(xx >> 1) * ld + pd(j)];
-    T val = coef * ((xx & 1) ? -z.y * inv : z.x * inv);
-    if (mult) val *= sm.mult[idx];
-    if (accumulate) val += sm.acc[idx];
-    out[base + j * S + xx] = val;
+    const cx<T> z = r2[(PAIR ? xx : (xx >> 1)) * ld + pd(j)];
+    io.out[base + j * S + xx] = deriv_out<T, PAIR>(io, sm, idx, plane, z, inv, (xx & 1) != 0);
   }
 }
 
@@ -368,8 +422,9 @@ k_r2c_rows(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, int 
   }
   __syncthreads();
   const cx<T>* r = run_fft<T, NC>(sm.a, sm.b, L, B, ld, plan, sm.tw);
-  for (int idx = threadIdx.x; idx < 2 * B * Lh; idx += blockDim.x) {
-    const int rr = idx / Lh, k = idx - rr * Lh;
+  StridedQR qr(threadIdx.x, Lh);
+  for (int idx = threadIdx.x; idx < 2 * B * Lh; idx += blockDim.x, qr.next()) {
+    const int rr = qr.q, k = qr.r;
     if (rr >= nrows) continue;
     const int p = rr >> 1;
     const cx<T> zk = r[p * ld + pd(k)];
@@ -398,8 +453,9 @@ k_c2r_rows(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, int 
   cpa_wait<0>();
   __syncthreads();
   // Z_k = A_k + i B_k (k < Lh) and Z_{L-k} = conj(A_k) + i conj(B_k); store conj(Z) in `a`.
-  for (int idx = threadIdx.x; idx < B * Lh; idx += blockDim.x) {
-    const int p = idx / Lh, k = idx - p * Lh;
+  StridedQR qr(threadIdx.x, Lh);
+  for (int idx = threadIdx.x; idx < B * Lh; idx += blockDim.x, qr.next()) {
+    const int p = qr.q, k = qr.r;
     const cx<T> A = (2 * p < nrows) ? stg[(2 * p) * Lh + k] : mk<T>(T(0), T(0));
     const cx<T> Bv = (2 * p + 1 < nrows) ? stg[(2 * p + 1) * Lh + k] : mk<T>(T(0), T(0));
     sm.a[p * ld + pd(k)] = cconj(mk<T>(A.x - Bv.y, A.y + Bv.x));
@@ -437,24 +493,27 @@ k_fft_cols(cx<T>* __restrict__ fh, int Lr, long long S, long long outer_stride, 
   const long long base = (long long)blockIdx.y * outer_stride + x0;
   const int valid = (nx - x0) < B ? (nx - x0) : B;
   // stage the tile as b[j * B + p]
-  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-    const int j = idx / B, p = idx - j * B;
-    if (p < valid) cpa_cx<T>(b + idx, fh + base + j * S + p);
+  {
+    StridedQR qr(threadIdx.x, B);
+    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x, qr.next())
+      if (qr.r < valid) cpa_cx<T>(b + idx, fh + base + qr.q * S + qr.r);
   }
   cpa_commit();
   load_tw<T>(tw, twg, L);
   cpa_wait<0>();
   __syncthreads();
-  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-    const int j = idx / B, p = idx - j * B;
+  StridedQR qa(threadIdx.x, B);
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x, qa.next()) {
+    const int j = qa.q, p = qa.r;
     cx<T> z = (p < valid) ? b[idx] : mk<T>(T(0), T(0));
     if (inverse) z = cconj(z);
     a[p * ld + pd(j)] = z;
   }
   __syncthreads();
   const cx<T>* r = run_fft<T, NC>(a, b, L, B, ld, plan, tw);
-  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-    const int j = idx / B, p = idx - j * B;
+  StridedQR qb(threadIdx.x, B);
+  for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x, qb.next()) {
+    const int j = qb.q, p = qb.r;
     if (p >= valid) continue;
     cx<T> z = r[p * ld + pd(j)];
     if (inverse) z = cscale(cconj(z), scale);
@@ -539,38 +598,39 @@ template <typename T> size_t deriv_smem_bytes(int L, int B) {
   return sizeof(cx<T>) * (twn + 2 * bufn) + 2 * sizeof(T) * 2 * (size_t)B * L;
 }
 
-template <typename T>
-cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult,
-                         T* out, T coef, bool accumulate, cudaStream_t st) {
+template <typename T, bool PAIR>
+static cudaError_t deriv_pass(const Grid& g, const FftTables<T>& ft, int axis, const DerivIO<T>& io, cudaStream_t st) {
   const int L = g.n[axis];
   if (L == 1) {  // a singleton axis carries only k = 0: the derivative is zero
-    if (accumulate) return cudaSuccess;
-    return cudaMemsetAsync(out, 0, sizeof(T) * g.nvox, st);
+    if (io.accumulate) return cudaSuccess;
+    return cudaMemsetAsync(io.out, 0, sizeof(T) * g.nvox, st);
   }
   int B = ft.deriv_pencils[axis] > 0 ? ft.deriv_pencils[axis] : deriv_batch<T>(L);
   const int ld = lead_dim(L);
   const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-  const bool ptrs16 = al(f) && al(out) && (!mult || al(mult));
+  const bool ptrs16 = al(io.f) && al(io.out) && (!io.mult || al(io.mult)) && (!PAIR || al(io.f2)) &&
+                      (!PAIR || !io.mult2 || al(io.mult2));
   constexpr int per = 16 / sizeof(T);
+  constexpr int rpc = PAIR ? 1 : 2;  // real pencils of one field per complex pencil
   if (axis == 2) {
     const long long rows = (long long)g.n[0] * g.n[1];
-    const long long pairs = (rows + 1) / 2;
-    if (B > pairs) B = (int)pairs;
+    const long long most = (rows + rpc - 1) / rpc;
+    if (B > most) B = (int)most;
     const size_t sm = deriv_smem_bytes<T>(L, B);
-    const long long grid = (rows + 2LL * B - 1) / (2LL * B);
+    const long long grid = (rows + (long long)rpc * B - 1) / ((long long)rpc * B);
     const int vec = (ptrs16 && (L % per) == 0) ? 1 : 0;
     return with_nc<T>(L, [&](auto nc) {
       constexpr int NC = decltype(nc)::value;
-      cudaError_t e = allow_smem(k_deriv_rows<T, NC>, sm);
+      cudaError_t e = allow_smem(k_deriv_rows<T, NC, PAIR>, sm);
       if (e != cudaSuccess) return e;
       note_launches(1);
-      k_deriv_rows<T, NC><<<(unsigned)grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, rows,
-                                                                 L, B, ld, ft.plan[2], ft.tw[2], vec);
+      k_deriv_rows<T, NC, PAIR><<<(unsigned)grid, kThreads, sm, st>>>(io, rows, L, B, ld, ft.plan[2], ft.tw[2], vec);
       return cudaGetLastError();
     });
   }
   const int nx = g.n[2];
-  if (2 * B > nx) B = (nx + 1) / 2;
+  if (rpc * B > nx) B = (nx + rpc - 1) / rpc;
+  const int W = rpc * B;
   const size_t sm = deriv_smem_bytes<T>(L, B);
   long long S, outer_stride;
   int outer;
@@ -584,17 +644,31 @@ cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const 
     outer_stride = nx;
   }
   // 16-byte chunks need whole chunks per tile row and 16-byte aligned row starts
-  const int vec = (ptrs16 && (2 * B) % per == 0 && (nx % per) == 0) ? 1 : 0;
-  dim3 grid((nx + 2 * B - 1) / (2 * B), outer);
+  const int vec = (ptrs16 && W % per == 0 && (nx % per) == 0) ? 1 : 0;
+  dim3 grid((nx + W - 1) / W, outer);
   return with_nc<T>(L, [&](auto nc) {
     constexpr int NC = decltype(nc)::value;
-    cudaError_t e = allow_smem(k_deriv_cols<T, NC>, sm);
+    cudaError_t e = allow_smem(k_deriv_cols<T, NC, PAIR>, sm);
     if (e != cudaSuccess) return e;
     note_launches(1);
-    k_deriv_cols<T, NC><<<grid, kThreads, sm, st>>>(f, mult, out, coef, accumulate ? 1 : 0, L, S, outer_stride,
-                                                     nx, B, ld, ft.plan[axis], ft.tw[axis], vec);
+    k_deriv_cols<T, NC, PAIR><<<grid, kThreads, sm, st>>>(io, L, S, outer_stride, nx, B, ld, ft.plan[axis],
+                                                           ft.tw[axis], vec);
     return cudaGetLastError();
   });
+}
+
+template <typename T>
+cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult,
+                         T* out, T coef, bool accumulate, cudaStream_t st) {
+  const DerivIO<T> io{f, mult, nullptr, nullptr, out, coef, T(0), accumulate ? 1 : 0};
+  return deriv_pass<T, false>(g, ft, axis, io, st);
+}
+
+template <typename T>
+cudaError_t launch_deriv_pair(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult, T coef,
+                              const T* f2, const T* mult2, T coef2, T* out, bool accumulate, cudaStream_t st) {
+  const DerivIO<T> io{f, mult, f2, mult2, out, coef, coef2, accumulate ? 1 : 0};
+  return deriv_pass<T, true>(g, ft, axis, io, st);
 }
 
 template <typename T>
@@ -689,6 +763,8 @@ template <typename T> bool deriv_pencils_fit(int L, int B) {
   template bool deriv_pencils_fit<T>(int, int);                                                     \
   template cudaError_t launch_deriv<T>(const Grid&, const FftTables<T>&, int, const T*, const T*, T*, T, \
                                        bool, cudaStream_t);                                          \
+  template cudaError_t launch_deriv_pair<T>(const Grid&, const FftTables<T>&, int, const T*, const T*, T,  \
+                                            const T*, const T*, T, T*, bool, cudaStream_t);          \
   template cudaError_t launch_r2c<T>(const Grid&, const FftTables<T>&, const T*, cx<T>*, cudaStream_t); \
   template cudaError_t launch_c2r<T>(const Grid&, const FftTables<T>&, cx<T>*, T*, cudaStream_t);
 GA_INST(float)

@@ -315,7 +315,7 @@ template <typename T> struct Engine : EngineBase {
   }
 
   // ---- profiling hooks ------------------------------------------------------------------------
-  enum { PROF_SL_FWD = 0, PROF_DERIV = 1, PROF_FFT = 2, PROF_SL_ADJ = 3 };
+  enum { PROF_SL_FWD = 0, PROF_DERIV = 1, PROF_FFT = 2, PROF_SL_ADJ = 3, PROF_DERIV_PAIR = 4 };
   void prof_begin(int cls) {
     if (prof_class != cls) return;
     if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
@@ -361,6 +361,13 @@ template <typename T> struct Engine : EngineBase {
     prof_begin(PROF_DERIV);
     ck(launch_deriv<T>(g, ft, axis, f, mult, out, (T)coef, acc, st), "deriv");
     prof_end(PROF_DERIV);
+  }
+  // out += coef mult d f + coef2 mult2 d f2 along `axis` (two time steps of the body force)
+  void deriv_pair(int axis, const T* f, const T* mult, double coef, const T* f2, const T* mult2, double coef2,
+                  T* out) {
+    prof_begin(PROF_DERIV_PAIR);
+    ck(launch_deriv_pair<T>(g, ft, axis, f, mult, (T)coef, f2, mult2, (T)coef2, out, true, st), "deriv pair");
+    prof_end(PROF_DERIV_PAIR);
   }
   void r2c(const T* f, cx<T>* fh) {
     prof_begin(PROF_FFT);
@@ -559,25 +566,47 @@ template <typename T> struct Engine : EngineBase {
 
   // Body force b (not projected) from the adjoint started at lam_init (lam_init may be lam[0]).
   // Requires departure points, mu and the forward states.
+  // The trapezoid rule over t_j = j h_t, j = n_t .. 0, visits the time steps in pairs (j, j - 1): the
+  // adjoint step to lambda_{j-1} is taken first, then one derivative pass per axis adds both steps'
+  // terms (the two fields share each complex FFT). With n_t even, j = 0 is a single pass.
   void body_force(const T* lam_init) {
     seg_base = -1;  // recompute every segment: the sequence of launches is the same on every call
     ck(cudaMemsetAsync(body, 0, sizeof(T) * vl, st), "memset body");
     const T* lcur = lam_init;
     int pp = (lam_init == lam[0]) ? 1 : 0;
-    for (int j = nt; j >= 0; --j) {
-      const T* mj = state(j);
-      const double coef = ht * ((j == 0 || j == nt) ? 0.5 : 1.0);
+    const bool cont = model == GA_MODEL_CONTINUITY;
+    auto coef_of = [&](int j) { return ht * ((j == 0 || j == nt) ? 0.5 : 1.0); };
+    int j = nt;
+    for (; j >= 1; j -= 2) {
+      const T* mj = state(j);  // a stored state, or in the same segment as j - 1
+      T* lprev = lam[pp];
+      sl_adjoint(lcur, lprev);  // lambda_{j-1}
+      pp ^= 1;
+      const T* mj1 = state(j - 1);
+      const double c0 = coef_of(j), c1 = coef_of(j - 1);
       for (int c = 0; c < dim; ++c) {
-        if (model == GA_MODEL_CONTINUITY)
-          deriv(g.axis_of(c), lcur, mj, body + c * nv, -coef, true);
-        else
-          deriv(g.axis_of(c), mj, lcur, body + c * nv, coef, true);
+        if (cont)  // b -= h_t w_j pi_j grad lambda_j
+          deriv_pair(g.axis_of(c), lcur, mj, -c0, lprev, mj1, -c1, body + c * nv);
+        else  // b += h_t w_j lambda_j grad m_j
+          deriv_pair(g.axis_of(c), mj, lcur, c0, mj1, lprev, c1, body + c * nv);
       }
-      if (j > 0) {
-        T* ldst = lam[pp];
-        sl_adjoint(lcur, ldst);
-        lcur = ldst;
+      if (j - 1 >= 1) {
+        T* lnext = lam[pp];
+        sl_adjoint(lprev, lnext);  // lambda_{j-2}
         pp ^= 1;
+        lcur = lnext;
+      } else {
+        lcur = lprev;
+      }
+    }
+    if (j == 0) {  // n_t even: the last time step alone
+      const T* m0s = state(0);
+      const double c0 = coef_of(0);
+      for (int c = 0; c < dim; ++c) {
+        if (cont)
+          deriv(g.axis_of(c), lcur, m0s, body + c * nv, -c0, true);
+        else
+          deriv(g.axis_of(c), m0s, lcur, body + c * nv, c0, true);
       }
     }
   }
@@ -1871,7 +1900,7 @@ ga_status ga_transport_vjp_exact(ga_ctx* ctx, const void* v, const void* gamma, 
 long long ga_kernel_launches(void) { return ga::g_launches.load(std::memory_order_relaxed); }
 
 ga_status ga_prof_start(ga_ctx* ctx, int kernel_class) {
-  if (!ctx || kernel_class < 0 || kernel_class > 3) return GA_ERR_ARG;
+  if (!ctx || kernel_class < 0 || kernel_class > 4) return GA_ERR_ARG;
   return dispatch(ctx, [&](auto& e) {
     if (e.prof_ev.empty()) {
       e.prof_ev.resize(4096);

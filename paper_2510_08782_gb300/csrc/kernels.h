@@ -33,6 +33,12 @@ template <typename T> struct FftTables {
 template <typename T>
 cudaError_t launch_deriv(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult,
                          T* out, T coef, bool accumulate, cudaStream_t st);
+// Two time steps of the body force in one pass: out (+)= coef mult d f + coef2 mult2 d f2 along
+// internal axis `axis`, formed as two successive launch_deriv calls would form it (mult, mult2 may be
+// null for 1). f and f2 share each complex FFT (real and imaginary parts).
+template <typename T>
+cudaError_t launch_deriv_pair(const Grid& g, const FftTables<T>& ft, int axis, const T* f, const T* mult, T coef,
+                              const T* f2, const T* mult2, T coef2, T* out, bool accumulate, cudaStream_t st);
 // Default pencils per CTA of a derivative pass of length L, and whether B pencils fit in one CTA's
 // shared memory on this device.
 template <typename T> int deriv_default_pencils(int L);

@@ -160,12 +160,12 @@ def test_state_and_adjoint_steps(shape, prec, model):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("model", ["advection", "continuity"])
-@pytest.mark.parametrize("ckpt", [0, 2])
+@pytest.mark.parametrize("ckpt,nt", [(0, 5), (2, 5), (2, 4), (3, 7)])
 @pytest.mark.parametrize("shape", [(32, 24), (16, 12, 20)])
-def test_body_force(shape, prec, model, ckpt):
+def test_body_force(shape, prec, model, ckpt, nt):
+    """The trapezoid sum over t_j visits the time steps in pairs sharing one derivative pass; odd and
+    even n_t (a single last step), with and without checkpoints (segments split across a pair)."""
     import paper_2510_08782_gb300 as ga
-
-    nt = 5
     P, m0, _, v = _problem(shape, prec, model=model, nt=nt, ckpt=ckpt)
     lam1 = quantise(random_fourier_field(shape, 1, 4, np.random.default_rng(5))[0], prec)
     b = empty(v.shape, prec)
