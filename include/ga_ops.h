@@ -41,13 +41,14 @@ ga_status ga_op_body_force(ga_ctx* ctx, const void* v, const void* lam1, void* b
 /* Spectral derivative along one axis (Sec. 2.2): df = F^{-1}[i k~_axis F f], k~ zero at Nyquist. */
 ga_status ga_op_deriv(ga_ctx* ctx, const void* f, int axis, void* df);
 
-/* Tile shapes of the context's FFT-derivative passes: pencils[a] is the number of pencil pairs one
- * CTA transforms along axis a (a = 0..dim-1, the descriptor's axis order). ga_setup picks them by
- * timing the default, its half and its double on the context's own grid (cached per precision and
- * grid for the process). No result depends on them. ga_op_set_tiles overrides them: a value of 0
- * restores the library default; GA_ERR_ARG if a value is negative or does not fit in one CTA's
- * shared memory. CUDA graphs the context recorded earlier keep the shapes they were recorded with.
- * pencils: HOST array of dim ints. */
+/* Tile shapes of the context's FFT-derivative passes: the number of complex pencils one CTA
+ * transforms. pencils[c] (c = 0..dim-1, the descriptor's axis order) is for the one-field passes
+ * along axis c (divergence, ga_op_deriv); pencils[dim + c] for the body force's passes that take two
+ * time steps at once. ga_setup picks each by timing the default, its half and its double on the
+ * context's own grid (cached per precision and grid for the process). No result depends on them.
+ * ga_op_set_tiles overrides them: a value of 0 restores the library default; GA_ERR_ARG if a value is
+ * negative or does not fit in one CTA's shared memory. CUDA graphs the context recorded earlier keep
+ * the shapes they were recorded with. pencils: HOST array of 2 * dim ints. */
 ga_status ga_op_get_tiles(const ga_ctx* ctx, int* pencils);
 ga_status ga_op_set_tiles(ga_ctx* ctx, const int* pencils);
 

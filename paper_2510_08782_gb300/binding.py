@@ -299,8 +299,9 @@ def ga_op_deriv(ctx, dtype, f, axis, df):
 
 
 def ga_op_get_tiles(ctx, dim):
-    """Pencil pairs per CTA of the FFT-derivative pass along each axis (chosen by the autotuner)."""
-    arr = (_c_int * dim)()
+    """Complex pencils per CTA of the FFT-derivative passes, chosen by the autotuner: dim values for the
+    one-field passes along each axis, then dim values for the body force's two-time-step passes."""
+    arr = (_c_int * (2 * dim))()
     _check(lib().ga_op_get_tiles(ctx, arr), ctx)
     return list(arr)
 

@@ -317,7 +317,7 @@ k_deriv_rows(DerivIO<T> io, long long rows, int Lr, int B, int ld, FftPlan plan,
       const T kt = ktilde<T>(k, L);
       return mk<T>(-kt * z.y, -kt * z.x);
     };
-    r = FusedForward<T, NC, 1, 8, false>::run(load, fin, sm.b, sm.a, B, ld, sm.tw);  // sm.b holds the raw block
+    r = FusedForward<T, NC, 1, 16, false>::run(load, fin, sm.b, sm.a, B, ld, sm.tw);  // sm.b holds the raw block
   } else {
     for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
       const int p = idx / L, j = idx - p * L;
@@ -328,7 +328,7 @@ k_deriv_rows(DerivIO<T> io, long long rows, int Lr, int B, int ld, FftPlan plan,
     mult_ik_conj<T>(r, B, L, ld);
   }
   cx<T>* o = (r == sm.a) ? sm.b : sm.a;
-  cx<T>* r2 = run_fft<T, NC, 8>(r, o, L, B, ld, plan, sm.tw);
+  cx<T>* r2 = run_fft<T, NC, 16>(r, o, L, B, ld, plan, sm.tw);
   cpa_wait<0>();
   __syncthreads();
   const T inv = T(1) / T(L);
@@ -377,7 +377,7 @@ k_deriv_cols(DerivIO<T> io, int Lr, long long S, long long outer_stride, int nx,
       const T kt = ktilde<T>(k, L);
       return mk<T>(-kt * z.y, -kt * z.x);
     };
-    r = FusedForward<T, NC, 1, 8, true>::run(load, fin, sm.b, sm.a, B, ld, sm.tw);  // sm.b holds the raw tile
+    r = FusedForward<T, NC, 1, 16, true>::run(load, fin, sm.b, sm.a, B, ld, sm.tw);  // sm.b holds the raw tile
   } else {
     StridedQR qr(threadIdx.x, B);
     for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x, qr.next()) sm.a[qr.r * ld + pd(qr.q)] = load(qr.r, qr.q);
@@ -386,7 +386,7 @@ k_deriv_cols(DerivIO<T> io, int Lr, long long S, long long outer_stride, int nx,
     mult_ik_conj<T>(r, B, L, ld);
   }
   cx<T>* o = (r == sm.a) ? sm.b : sm.a;
-  cx<T>* r2 = run_fft<T, NC, 8>(r, o, L, B, ld, plan, sm.tw);
+  cx<T>* r2 = run_fft<T, NC, 16>(r, o, L, B, ld, plan, sm.tw);
   cpa_wait<0>();
   __syncthreads();
   const T inv = T(1) / T(L);
@@ -605,7 +605,8 @@ static cudaError_t deriv_pass(const Grid& g, const FftTables<T>& ft, int axis, c
     if (io.accumulate) return cudaSuccess;
     return cudaMemsetAsync(io.out, 0, sizeof(T) * g.nvox, st);
   }
-  int B = ft.deriv_pencils[axis] > 0 ? ft.deriv_pencils[axis] : deriv_batch<T>(L);
+  const int tuned = PAIR ? ft.pair_pencils[axis] : ft.deriv_pencils[axis];
+  int B = tuned > 0 ? tuned : deriv_batch<T>(L);
   const int ld = lead_dim(L);
   const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   const bool ptrs16 = al(io.f) && al(io.out) && (!io.mult || al(io.mult)) && (!PAIR || al(io.f2)) &&

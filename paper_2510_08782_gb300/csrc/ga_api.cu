@@ -270,45 +270,58 @@ template <typename T> struct Engine : EngineBase {
   }
 
   // ---- tile autotuner --------------------------------------------------------------------------
-  // The FFT-derivative passes (two thirds of the body force's launches) take their tile shape, the
-  // number of pencils a CTA transforms, from timing: for each axis the default and its half and double
-  // are run on this context's own fields (m0 differentiated, times m1, accumulated into a scratch
-  // field), the fastest kept. Choices are cached per (precision, grid) for the process. Each pencil is
-  // transformed on its own, so no result depends on the choice.
+  // The FFT-derivative passes take their tile shape, the number of complex pencils a CTA transforms,
+  // from timing: for each axis, and separately for the one-field passes (div v) and the two-time-step
+  // passes of the body force, the default, its half and its double are run on this context's own fields
+  // (m0 differentiated, times m1, accumulated into a scratch field) and the fastest is kept. Choices
+  // are cached per (precision, grid) for the process. Each pencil is transformed on its own, so no
+  // result depends on the choice.
   void autotune_tiles() {
     static std::mutex mu;
-    static std::map<std::vector<int>, std::array<int, 3>> cache;
+    static std::map<std::vector<int>, std::array<int, 6>> cache;
     const std::vector<int> key = {(int)sizeof(T), g.n[0], g.n[1], g.n[2]};
     {
       std::lock_guard<std::mutex> lk(mu);
       auto it = cache.find(key);
       if (it != cache.end()) {
-        for (int a = 0; a < 3; ++a) ft.deriv_pencils[a] = it->second[a];
+        for (int a = 0; a < 3; ++a) {
+          ft.deriv_pencils[a] = it->second[a];
+          ft.pair_pencils[a] = it->second[3 + a];
+        }
         return;
       }
     }
-    std::array<int, 3> best = {0, 0, 0};
-    for (int a = 3 - dim; a < 3; ++a) {
-      const int L = g.n[a];
-      if (L == 1) continue;
-      const int b0 = deriv_default_pencils<T>(L);
-      float best_ms = 0.f;
-      for (int cand : {b0, b0 / 2, 2 * b0}) {
-        if (!deriv_pencils_fit<T>(L, cand)) continue;
-        ft.deriv_pencils[a] = cand;
-        ck(launch_deriv<T>(g, ft, a, m0, m1, tmp[0], T(1), false, st), "tuning pass");  // loads the kernel
-        ck(cudaEventRecord(ev[0], st), "event");
-        for (int r = 0; r < 3; ++r) ck(launch_deriv<T>(g, ft, a, m0, m1, tmp[0], T(1), true, st), "tuning pass");
-        ck(cudaEventRecord(ev[1], st), "event");
-        ck(cudaEventSynchronize(ev[1]), "event sync");
-        float ms = 0.f;
-        ck(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
-        if (best[a] == 0 || ms < best_ms) {
-          best[a] = cand;
-          best_ms = ms;
+    std::array<int, 6> best = {0, 0, 0, 0, 0, 0};
+    for (int pair = 0; pair < 2; ++pair) {
+      for (int a = 3 - dim; a < 3; ++a) {
+        const int L = g.n[a];
+        if (L == 1) continue;
+        int* slot = pair ? &ft.pair_pencils[a] : &ft.deriv_pencils[a];
+        const int b0 = deriv_default_pencils<T>(L);
+        float best_ms = 0.f;
+        int choice = 0;
+        for (int cand : {b0, b0 / 2, 2 * b0}) {
+          if (!deriv_pencils_fit<T>(L, cand)) continue;
+          *slot = cand;
+          auto pass = [&](bool acc) {
+            if (pair) ck(launch_deriv_pair<T>(g, ft, a, m0, m1, T(1), m1, m0, T(1), tmp[0], acc, st), "tuning pass");
+            else ck(launch_deriv<T>(g, ft, a, m0, m1, tmp[0], T(1), acc, st), "tuning pass");
+          };
+          pass(false);  // loads the kernel
+          ck(cudaEventRecord(ev[0], st), "event");
+          for (int r = 0; r < 3; ++r) pass(true);
+          ck(cudaEventRecord(ev[1], st), "event");
+          ck(cudaEventSynchronize(ev[1]), "event sync");
+          float ms = 0.f;
+          ck(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
+          if (choice == 0 || ms < best_ms) {
+            choice = cand;
+            best_ms = ms;
+          }
         }
+        *slot = choice;
+        best[3 * pair + a] = choice;
       }
-      ft.deriv_pencils[a] = best[a];
     }
     std::lock_guard<std::mutex> lk(mu);
     cache.emplace(key, best);
@@ -431,14 +444,27 @@ template <typename T> struct Engine : EngineBase {
     return cur;
   }
 
+  // First state index of the last checkpoint segment that has unstored states (they are recomputed in
+  // the backward sweep), or -1 when there is none.
+  int last_segment() const {
+    if (K <= 1 || (nt - 1) % K == 0) return -1;
+    return ((nt - 1) / K) * K;
+  }
+  // State solve storing the checkpoints. The unstored states of the last segment go straight to the
+  // segment buffer, where the backward sweep, which starts there, finds them: that segment is never
+  // recomputed.
   void forward_all() {
     const T* cur = m0;
+    const int jl = last_segment();
     for (int j = 0; j < nt; ++j) {
-      T* dst = stored(j + 1) ? const_cast<T*>(slot(j + 1)) : tmp[(j + 1) & 1];
+      T* dst;
+      if (stored(j + 1)) dst = const_cast<T*>(slot(j + 1));
+      else if (jl >= 0 && j + 1 > jl) dst = seg + (long long)(j - jl) * nv;
+      else dst = tmp[(j + 1) & 1];
       sl_forward(cur, dst);
       cur = dst;
     }
-    seg_base = -1;
+    seg_base = jl;
   }
 
   const T* state(int j) {
@@ -569,8 +595,10 @@ template <typename T> struct Engine : EngineBase {
   // The trapezoid rule over t_j = j h_t, j = n_t .. 0, visits the time steps in pairs (j, j - 1): the
   // adjoint step to lambda_{j-1} is taken first, then one derivative pass per axis adds both steps'
   // terms (the two fields share each complex FFT). With n_t even, j = 0 is a single pass.
+  // Precondition: the last forward_all ran on the same velocity (its last segment is in the segment
+  // buffer; a captured launch sequence therefore never depends on host state left by other calls).
   void body_force(const T* lam_init) {
-    seg_base = -1;  // recompute every segment: the sequence of launches is the same on every call
+    seg_base = last_segment();
     ck(cudaMemsetAsync(body, 0, sizeof(T) * vl, st), "memset body");
     const T* lcur = lam_init;
     int pp = (lam_init == lam[0]) ? 1 : 0;
@@ -732,7 +760,7 @@ template <typename T> struct Engine : EngineBase {
     ck(cudaMemsetAsync(G, 0, sizeof(T) * vl, st), "memset G");
     if (rT != lam[0]) ck(cudaMemcpyAsync(lam[0], rT, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st), "copy r");
     int pp = 0;
-    seg_base = -1;
+    seg_base = last_segment();  // dto_forward ran just before on the same v
     for (int j = nt - 1; j >= 0; --j) {
       const T* mj = state(j);
       ck(launch_dto_accum<T>(g, lam[pp], mj, xm, G, (T)coef, st), "dto accumulate");
@@ -1741,33 +1769,38 @@ ga_status ga_op_deriv(ga_ctx* ctx, const void* f, int axis, void* df) {
   });
 }
 
+// pencils[c] (c < dim): one-field passes along axis c; pencils[dim + c]: two-time-step passes.
 ga_status ga_op_get_tiles(const ga_ctx* ctx, int* pencils) {
   if (!ctx || !pencils) return GA_ERR_ARG;
   const int dim = ctx->desc.dim;
-  for (int c = 0; c < dim; ++c) {
-    const int a = 3 - dim + c;
-    const int L = ctx->desc.n[c];
-    const int p = ctx->ef ? ctx->ef->ft.deriv_pencils[a] : ctx->ed->ft.deriv_pencils[a];
-    pencils[c] = p > 0 ? p : (ctx->ef ? ga::deriv_default_pencils<float>(L) : ga::deriv_default_pencils<double>(L));
-  }
+  for (int pair = 0; pair < 2; ++pair)
+    for (int c = 0; c < dim; ++c) {
+      const int a = 3 - dim + c;
+      const int L = ctx->desc.n[c];
+      const int p = ctx->ef ? (pair ? ctx->ef->ft.pair_pencils[a] : ctx->ef->ft.deriv_pencils[a])
+                            : (pair ? ctx->ed->ft.pair_pencils[a] : ctx->ed->ft.deriv_pencils[a]);
+      pencils[pair * dim + c] =
+          p > 0 ? p : (ctx->ef ? ga::deriv_default_pencils<float>(L) : ga::deriv_default_pencils<double>(L));
+    }
   return GA_OK;
 }
 
 ga_status ga_op_set_tiles(ga_ctx* ctx, const int* pencils) {
   if (!ctx || !pencils) return GA_ERR_ARG;
   const int dim = ctx->desc.dim;
-  for (int c = 0; c < dim; ++c) {
-    const int L = ctx->desc.n[c];
-    const bool fits = ctx->ef ? ga::deriv_pencils_fit<float>(L, pencils[c]) : ga::deriv_pencils_fit<double>(L, pencils[c]);
-    if (pencils[c] < 0 || (pencils[c] > 0 && !fits)) {
-      set_err(ctx, "ga_op_set_tiles: %d pencils per CTA along axis %d do not fit", pencils[c], c);
+  for (int i = 0; i < 2 * dim; ++i) {
+    const int L = ctx->desc.n[i % dim];
+    const bool fits = ctx->ef ? ga::deriv_pencils_fit<float>(L, pencils[i]) : ga::deriv_pencils_fit<double>(L, pencils[i]);
+    if (pencils[i] < 0 || (pencils[i] > 0 && !fits)) {
+      set_err(ctx, "ga_op_set_tiles: %d pencils per CTA along axis %d do not fit", pencils[i], i % dim);
       return GA_ERR_ARG;
     }
   }
-  for (int c = 0; c < dim; ++c) {
-    const int a = 3 - dim + c;
-    if (ctx->ef) ctx->ef->ft.deriv_pencils[a] = pencils[c];
-    else ctx->ed->ft.deriv_pencils[a] = pencils[c];
+  for (int i = 0; i < 2 * dim; ++i) {
+    const int a = 3 - dim + i % dim;
+    int* dst = ctx->ef ? (i < dim ? ctx->ef->ft.deriv_pencils : ctx->ef->ft.pair_pencils)
+                       : (i < dim ? ctx->ed->ft.deriv_pencils : ctx->ed->ft.pair_pencils);
+    dst[a] = pencils[i];
   }
   return GA_OK;
 }

@@ -26,6 +26,7 @@ template <typename T> struct FftTables {
   // pencils per CTA of the derivative pass along each internal axis (0: deriv_default_pencils); the
   // tile holds 2 B real pencils. Chosen per context by timing; no result depends on it.
   int deriv_pencils[3] = {0, 0, 0};
+  int pair_pencils[3] = {0, 0, 0};  // the same for the two-time-step passes of the body force
 };
 
 // ---- spectral / FFT passes (fft_kernels.cu) --------------------------------------------------

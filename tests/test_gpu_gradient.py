@@ -74,17 +74,26 @@ def test_gradient_with_a_512_axis(prec, model):
     assert rel_l2(host(g), gref) < tol, (rel_l2(host(g), gref), tol)
 
 
-@pytest.mark.parametrize("ckpt", [1, 3, 4])
-def test_checkpointed_gradient_equals_stored(ckpt):
+@pytest.mark.parametrize("prec,nt,ckpt", [("fp64", 7, 1), ("fp64", 7, 3), ("fp64", 7, 4), ("mixed", 16, 4),
+                                          ("mixed", 9, 4), ("mixed", 10, 3)])
+def test_checkpointed_gradient_equals_stored(prec, nt, ckpt):
+    """Checkpoints every K steps; the backward sweep recomputes each segment but the last, whose states
+    the forward sweep left in the segment buffer. Recomputation repeats the same kernels on the same
+    inputs, so the gradient is bitwise that of the stored trajectory (also through the solver's reuse
+    of a line-search state solve)."""
     shape = (16, 12, 20)
-    P0, O, v = _setup(shape, "fp64", "continuity", nt=7, s=1)
-    Pk, _, _ = _setup(shape, "fp64", "continuity", nt=7, s=1, ckpt=ckpt)
-    g0, gk = empty(v.shape, "fp64"), empty(v.shape, "fp64")
-    J0 = P0.gradient(to_dev(v, "fp64"), g0)
-    Jk = Pk.gradient(to_dev(v, "fp64"), gk)
-    # recomputation repeats the same kernels on the same inputs: bitwise identical
+    P0, O, v = _setup(shape, prec, "continuity", nt=nt, s=1)
+    Pk, _, _ = _setup(shape, prec, "continuity", nt=nt, s=1, ckpt=ckpt)
+    g0, gk = empty(v.shape, prec), empty(v.shape, prec)
+    J0 = P0.gradient(to_dev(v, prec), g0)
+    Jk = Pk.gradient(to_dev(v, prec), gk)
     assert J0 == Jk
     assert np.array_equal(host(g0), host(gk))
+    v0 = to_dev(np.zeros_like(v), prec)
+    vk = to_dev(np.zeros_like(v), prec)
+    for _ in range(3):
+        s0, sk = P0.step(v0), Pk.step(vk)
+        assert np.array_equal(host(v0), host(vk)) and s0.obj == sk.obj
 
 
 def test_host_buffers_match_device_buffers():

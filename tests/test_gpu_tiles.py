@@ -37,7 +37,7 @@ def test_every_tile_candidate_gives_identical_results(shape, prec):
     P, v, m0 = _problem(shape, prec)
     dim = len(shape)
     tuned = ga_op_get_tiles(P.ctx, dim)
-    ga_op_set_tiles(P.ctx, [0] * dim)
+    ga_op_set_tiles(P.ctx, [0] * (2 * dim))
     default = ga_op_get_tiles(P.ctx, dim)
     for t, d in zip(tuned, default):
         assert t in (d, max(d // 2, 1), 2 * d), (tuned, default)
@@ -62,7 +62,7 @@ def test_every_tile_candidate_gives_identical_results(shape, prec):
 
     ref = run()
     for k in range(3):
-        for a in range(dim):
+        for a in range(2 * dim):  # one-field passes, then the body force's two-time-step passes
             tiles = list(default)
             tiles[a] = [default[a], max(default[a] // 2, 1), 2 * default[a]][k]
             try:
@@ -79,7 +79,8 @@ def test_set_tiles_rejects_bad_shapes():
 
     P, _, _ = _problem((32, 32, 32), "mixed")
     before = ga_op_get_tiles(P.ctx, 3)
-    for bad in ([-1, 0, 0], [0, 4096, 0]):
+    assert len(before) == 6
+    for bad in ([-1, 0, 0, 0, 0, 0], [0, 4096, 0, 0, 0, 0], [0, 0, 0, 0, 0, -2]):
         with pytest.raises(GaError) as e:
             ga_op_set_tiles(P.ctx, bad)
         assert e.value.status == 1
