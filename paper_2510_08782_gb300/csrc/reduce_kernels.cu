@@ -78,13 +78,32 @@ __device__ __forceinline__ double block_max(double x) {
 }
 
 // Per-CTA partial sums of <a, b_k> for k < count (count <= NB).
+// Each thread visits i, i + stride, i + 2 stride, ... in order; U consecutive visits load their
+// operands before any of them is accumulated, so (1 + count) U loads are in flight per thread while
+// every accumulator still receives its products in the same order.
 template <typename T, int NB>
 __device__ __forceinline__ void dots_body(const T* __restrict__ a, const T* const* b, int count, long long len,
                                           double* __restrict__ partial) {
   using Acc = typename AccOf<T>::type;
+  constexpr int U = NB <= 4 ? 4 : (NB <= 8 ? 2 : 1);
   Acc acc[NB];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (U - 1) * stride < len; i += U * stride) {
+    T av[U], bv[U][NB];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      av[u] = a[i + u * stride];
+#pragma unroll
+      for (int k = 0; k < NB; ++k) bv[u][k] = k < count ? b[k][i + u * stride] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k < count) acc[k].add_prod(av[u], bv[u][k]);
+  }
+  for (; i < len; i += stride) {
     const T av = a[i];
 #pragma unroll
     for (int k = 0; k < NB; ++k)
@@ -135,12 +154,23 @@ k_dots_ring(const T* __restrict__ a, const T* __restrict__ first, const T* __res
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_maxabs(const T* __restrict__ x, long long len, double* __restrict__ partial) {
-  T m = T(0);  // max of |x| is exact in the element type
+  T m = T(0);  // max of |x| is exact in the element type (and independent of the visiting order)
   int bad = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < len; i += 4 * stride) {  // four loads in flight per thread
+    T v4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v4[u] = fabs(x[i + u * stride]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!(v4[u] <= T(3.0e38))) bad = 1;  // NaN or Inf
+      else m = v4[u] > m ? v4[u] : m;
+    }
+  }
+  for (; i < len; i += stride) {
     const T v = fabs(x[i]);
-    if (!(v <= T(3.0e38))) bad = 1;  // NaN or Inf
+    if (!(v <= T(3.0e38))) bad = 1;
     else m = v > m ? v : m;
   }
   const int anybad = __syncthreads_or(bad);
