@@ -372,12 +372,17 @@ __global__ void __launch_bounds__(256, 4) k_sl_tile1(const float* __restrict__ f
 
 // RK2 departure points (displacements in cells) for 3D FP32 grids: X* = x -/+ h_t v(x), then
 // X-/+ = x -/+ (h_t / 2)(v(x) + I[v](X*)). The three velocity components of the brick + halo are
-// staged in shared memory; the three interpolants at X* share one stencil.
+// staged in shared memory; the three interpolants at X* share one stencil. Each thread walks its
+// column two voxels at a time: a pair's weights and its 64-tap sums run as packed FP32x2 operations
+// (interp64, as in the state steps). A voxel done alone (odd column length, or a stencil beyond the
+// halo in the pair) repeats the same operations in scalar form, so its value does not depend on the
+// pairing.
 __global__ void __launch_bounds__(256, 2)
 k_departure_tile(const float* __restrict__ v, float* __restrict__ xm, float* __restrict__ xp, int n0, int n1, int n2,
                  float ht, int both, int vec) {
   extern __shared__ __align__(16) float smem[];
   const long long nv = (long long)n0 * n1 * n2;
+  const long long plane = (long long)n1 * n2;
   const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
   const BrickIdx bi = brick_of(blockIdx.x, nbx, nby);
   for (int c = 0; c < 3; ++c) stage_async(smem + c * TILEA, v + c * nv, bi, n0, n1, n2, vec != 0);
@@ -390,54 +395,80 @@ k_departure_tile(const float* __restrict__ v, float* __restrict__ xm, float* __r
   __syncthreads();
   if (gx >= n2 || gy >= n1) return;
   const int nz = min(BZ, n0 - bi.bz * BZ);
-#pragma unroll 1
-  for (int vz = 0; vz < nz; ++vz) {
-    const long long idx = ((long long)(bi.bz * BZ + vz) * n1 + gy) * n2 + gx;
-    const int center = ((vz + H + 1) * TY + warp + H + 1) * TXA + lane + XOFF;
-    float vc[3];
+  const long long idx0 = ((long long)(bi.bz * BZ) * n1 + gy) * n2 + gx;
+  // tile index of (z = 0, y, x) minus the stencil's first-tap offset
+  const int col = (warp + H) * TXA + lane + XOFF - 1;
+  auto center = [&](int vz, int k) { return smem[k * TILEA + ((vz + H + 1) * TY + warp + H + 1) * TXA + lane + XOFF]; };
+  // one voxel alone
+  auto single = [&](int vz, float sign, float* o) {
+    const long long idx = idx0 + vz * plane;
+    float d[3], vc[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vc[c] = smem[c * TILEA + center];
+    for (int k = 0; k < 3; ++k) {
+      vc[k] = center(vz, k);
+      d[k] = -sign * ht * vc[k] * ih[k];
+    }
+    const float fz = floorf(d[0]), fy = floorf(d[1]), fx = floorf(d[2]);
+    if (in_halo(fz, fy, fx)) {
+      float wz[4], wy[4], wx[4];
+      lagrange4v(d[0] - fz, wz);
+      lagrange4v(d[1] - fy, wy);
+      lagrange4v(d[2] - fx, wx);
+      const int base = col + ((vz + H + (int)fz) * TY + (int)fy) * TXA + (int)fx;
 #pragma unroll 1
-    for (int sg = 0; sg < (both ? 2 : 1); ++sg) {
-      const float sign = sg == 0 ? 1.f : -1.f;
-      float* o = sg == 0 ? xm : xp;
-      const float dz = -sign * ht * vc[0] * ih[0], dy = -sign * ht * vc[1] * ih[1], dx = -sign * ht * vc[2] * ih[2];
-      const float fz = floorf(dz), fy = floorf(dy), fx = floorf(dx);
-      if (fz >= -H && fz <= H - 1 && fy >= -H && fy <= H - 1 && fx >= -H && fx <= H - 1) {
-        float wz[4], wy[4], wx[4];
-        lagrange4(dz - fz, wz);
-        lagrange4(dy - fy, wy);
-        lagrange4(dx - fx, wx);
-        const int base = ((vz + H + (int)fz) * TY + warp + H + (int)fy) * TXA + lane + XOFF - 1 + (int)fx;
+      for (int k = 0; k < 3; ++k) {
+        const float* t = smem + k * TILEA + base;
+        const float acc = interp64<TXA, float>(wz, wy, wx, [&](int q) { return t[q]; });
+        o[k * nv + idx] = -sign * 0.5f * ht * (vc[k] + acc) * ih[k];
+      }
+    } else {
 #pragma unroll 1
-        for (int k = 0; k < 3; ++k) {  // one component at a time: the stencil weights are shared
-          const float* t = smem + k * TILEA + base;
-          float acc = 0.f;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float ay = 0.f;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const float* r = t + (c * TY + b) * TXA;
-              ay += wy[b] * (wx[0] * r[0] + wx[1] * r[1] + wx[2] * r[2] + wx[3] * r[3]);
-            }
-            acc += wz[c] * ay;
-          }
-          const float vk = k == 0 ? vc[0] : (k == 1 ? vc[1] : vc[2]);
-          const float ihk = k == 0 ? ih[0] : (k == 1 ? ih[1] : ih[2]);
-          o[k * nv + idx] = -sign * 0.5f * ht * (vk + acc) * ihk;
-        }
-      } else {
-#pragma unroll 1
-        for (int k = 0; k < 3; ++k) {
-          float P, S;
-          gather_global<1>(v + k * nv, nullptr, bi.bz * BZ + vz, gy, gx, dz, dy, dx, n0, n1, n2, P, S);
-          const float vk = k == 0 ? vc[0] : (k == 1 ? vc[1] : vc[2]);
-          const float ihk = k == 0 ? ih[0] : (k == 1 ? ih[1] : ih[2]);
-          o[k * nv + idx] = -sign * 0.5f * ht * (vk + P) * ihk;
-        }
+      for (int k = 0; k < 3; ++k) {
+        float P, S;
+        gather_global<1>(v + k * nv, nullptr, bi.bz * BZ + vz, gy, gx, d[0], d[1], d[2], n0, n1, n2, P, S);
+        o[k * nv + idx] = -sign * 0.5f * ht * (vc[k] + P) * ih[k];
       }
     }
+  };
+#pragma unroll 1
+  for (int sg = 0; sg < (both ? 2 : 1); ++sg) {
+    const float sign = sg == 0 ? 1.f : -1.f;
+    float* o = sg == 0 ? xm : xp;
+    int vz = 0;
+#pragma unroll 1
+    for (; vz + 1 < nz; vz += 2) {
+      float da[3], db[3], ca[3], cb[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ca[k] = center(vz, k);
+        cb[k] = center(vz + 1, k);
+        da[k] = -sign * ht * ca[k] * ih[k];
+        db[k] = -sign * ht * cb[k] * ih[k];
+      }
+      const float fza = floorf(da[0]), fya = floorf(da[1]), fxa = floorf(da[2]);
+      const float fzb = floorf(db[0]), fyb = floorf(db[1]), fxb = floorf(db[2]);
+      if (in_halo(fza, fya, fxa) && in_halo(fzb, fyb, fxb)) {
+        float2 wz[4], wy[4], wx[4];
+        lagrange4v(make_float2(da[0] - fza, db[0] - fzb), wz);
+        lagrange4v(make_float2(da[1] - fya, db[1] - fyb), wy);
+        lagrange4v(make_float2(da[2] - fxa, db[2] - fxb), wx);
+        const int ba = col + ((vz + H + (int)fza) * TY + (int)fya) * TXA + (int)fxa;
+        const int bb = col + ((vz + 1 + H + (int)fzb) * TY + (int)fyb) * TXA + (int)fxb;
+        const long long ia = idx0 + vz * plane, ib = ia + plane;
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) {
+          const float* t = smem + k * TILEA;
+          const float2 acc =
+              interp64<TXA, float2>(wz, wy, wx, [&](int q) { return make_float2(t[ba + q], t[bb + q]); });
+          o[k * nv + ia] = -sign * 0.5f * ht * (ca[k] + acc.x) * ih[k];
+          o[k * nv + ib] = -sign * 0.5f * ht * (cb[k] + acc.y) * ih[k];
+        }
+      } else {
+        single(vz, sign, o);
+        single(vz + 1, sign, o);
+      }
+    }
+    if (vz < nz) single(vz, sign, o);
   }
 }
 
