@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(libga):
     # and the binding wraps each of them under the same name
     import paper_2510_08782_gb300 as pkg
 
-    unwrapped = [n for n in sorted(names) if n != "ga_get_stats" and not hasattr(pkg, n)]
+    unwrapped = [n for n in sorted(names) if not hasattr(pkg, n)]
     assert not unwrapped, unwrapped
 
 
@@ -98,6 +98,20 @@ def test_null_arguments_rejected(libga):
     assert L.ga_transport_vjp_exact(None, None, None, None, 0) == 1
     assert L.ga_solve_batch(-1, None, None, 0, None) == 1
     assert L.ga_setup(None, None, None, None, 0, None, None) == 1
+    tiles = (ctypes.c_int * 6)()
+    assert L.ga_op_get_tiles(None, tiles) == 1
+    assert L.ga_op_set_tiles(None, tiles) == 1
+    assert L.ga_prof_start(None, 4) == 1
+    assert L.ga_get_stats(None, None) == 1
+
+
+def test_binding_rejects_unknown_graph_mode(libga):
+    """Problem() checks its graph mode before it touches the device."""
+    from paper_2510_08782_gb300 import Problem
+
+    m = np.zeros((16, 16))
+    with pytest.raises(ValueError):
+        Problem(m, m, nt=2, graphs="sometimes")
 
 
 def test_binding_rejects_wrong_dtype(libga):
