@@ -56,6 +56,24 @@ def test_fft_r2c_and_inverse(shape, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", [(32, 24), (16, 12, 20), (64, 48, 40)])
+def test_fft_matches_cufft(shape, prec):
+    """Cross-check of the hand-written real FFT against cuFFT (through torch.fft) on the same device
+    data; cuFFT serves only as this check."""
+    import torch
+
+    import paper_2510_08782_gb300 as ga
+
+    P, _, _, _ = _problem(shape, prec)
+    f = quantise(random_fourier_field(shape, 1, max(shape) // 2, np.random.default_rng(4))[0], prec)
+    fd = to_dev(f, prec)
+    fh = empty(shape[:-1] + (shape[-1] // 2 + 1, 2), prec)
+    ga.ga_op_fft_r2c(P.ctx, P.dtype, fd, fh)
+    ref = torch.view_as_real(torch.fft.rfftn(fd)).cpu().numpy()
+    assert rel_l2(host(fh), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", SHAPES)
 def test_spectral_derivative_and_divergence(shape, prec):
     import paper_2510_08782_gb300 as ga
