@@ -230,7 +230,41 @@ def run_sweep(args):
         del v
         return row
 
-    rows = {"hyper": [], "alpha": [], "mesh": []}
+    def solve_inc(window, sigma, tau, method="ga-ngmres"):
+        """One solve of the incompressible stand-in of Sec. 3.6 (2D 256^2 sinusoidal images, H3,
+        alpha = 1e-4, n_t = 16, tolerance 1e-3) in FP64, with det grad y of the solution."""
+        if "inc" not in data:
+            w = workload("inc2d256", seed=0)
+            data["inc"] = (w, torch.from_numpy(w["m0"]).cuda(), torch.from_numpy(w["m1"]).cuda())
+        w, m0, m1 = data["inc"]
+        P = ga.Problem(m0, m1, nt=w["nt"], model="incompressible", reg_order=w["reg_order"], alpha=w["alpha"],
+                       prec="fp64", window=window, sigma=sigma, tau=tau, max_iter=200, rel_tol=w["rel_tol"],
+                       method=method)
+        v = torch.zeros((2,) + tuple(w["n"]), dtype=torch.float64, device="cuda")
+        mis0 = P.objective(v)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        err = None
+        try:
+            st, _ = P.solve(v)
+        except ga.GaError as e:
+            err = str(e)
+            st = P.stats()
+        torch.cuda.synchronize()
+        tts = time.perf_counter() - t0
+        u = torch.empty_like(v)
+        jd = torch.empty(tuple(w["n"]), dtype=torch.float64, device="cuda")
+        P.deformation(v, u, jd)
+        row = {"n": list(w["n"]), "nt": w["nt"], "alpha": w["alpha"], "w": window, "p": [sigma, tau],
+               "method": method, "iters": st.iters, "grad_evals": st.grad_evals, "obj_evals": st.obj_evals,
+               "pde_solves": st.pde_solves, "converged": bool(st.converged), "grad": st.rel_grad_inf,
+               "dist": st.mismatch / mis0 if mis0 > 0 else None, "tts_s": tts,
+               "det_min": float(jd.min()), "det_mean": float(jd.mean()), "det_max": float(jd.max()),
+               "det_std": float(jd.std()), "error": err}
+        P.close()
+        return row
+
+    rows = {"hyper": [], "alpha": [], "mesh": [], "inc": []}
     t_all = time.perf_counter()
     tol = args.sweep_tol  # the paper's default tolerance is 5e-2 (Sec. 3.1)
     if "hyper" in parts:  # Sec. 3.3: n = 128, n_t = 8, alpha = 1e-3
@@ -252,18 +286,26 @@ def run_sweep(args):
             rows["mesh"].append(solve(n, nt, 1e-3, 25, 4, 2, 1e-3))
             data.pop(n, None)
             torch.cuda.empty_cache()
+    if "inc" in parts:  # Sec. 3.6: incompressible flow, H3
+        for w in (5, 10, 25):
+            for sg, ta in ((4, 2), (5, 1), (2, 4)):
+                rows["inc"].append(solve_inc(w, sg, ta))
+        rows["inc"].append(solve_inc(0, 1, 0, method="rpgd"))
     total_s = time.perf_counter() - t_all
     if rank != 0:
         return 0
-    allrows = rows["hyper"] + rows["alpha"] + rows["mesh"]
+    allrows = rows["hyper"] + rows["alpha"] + rows["mesh"] + rows["inc"]
     conv = sum(r["converged"] for r in allrows)
     print(json.dumps({
-        "metric": "configuration sweep: iterations and time to rel-grad per configuration (3D advection, H2)",
+        "metric": "configuration sweep: iterations and time to rel-grad per configuration (3D advection H2; "
+                  "2D incompressible H3)",
         "value": conv, "unit": "converged runs", "n_gpus": 1, "steps": len(allrows), "warmup": 0,
         "ms_per_step": 1e3 * total_s / max(len(allrows), 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "sweep: adv3d64 recipe; hyperparameters and alpha at 128^3 (n_t = 8), "
-                               "mesh 64..512 with n_t = n/16", "tol": args.sweep_tol, "mesh_tol": 1e-3},
+                               "mesh 64..512 with n_t = n/16; incompressible: inc2d256 recipe (2D 256^2 "
+                               "sinusoidal images, n_t = 16, H3, alpha = 1e-4, FP64)",
+                   "tol": args.sweep_tol, "mesh_tol": 1e-3, "inc_tol": 1e-3},
         "gpu_launches": ga.ga_kernel_launches(), "sweep": rows}))
     return 0
 
@@ -361,8 +403,8 @@ def main():
                     help="skip the device-driven (one graph launch) time-to-solution")
     ap.add_argument("--prof-class", type=int, default=PROF_SL_FWD)
     ap.add_argument("--grid", type=int, default=N, help="grid size (default 256; smaller only for smoke runs)")
-    ap.add_argument("--sweep-parts", default="hyper,alpha,mesh",
-                    help="--workload sweep: comma-separated subset of hyper, alpha, mesh")
+    ap.add_argument("--sweep-parts", default="hyper,alpha,mesh,inc",
+                    help="--workload sweep: comma-separated subset of hyper, alpha, mesh, inc")
     ap.add_argument("--sweep-max-n", type=int, default=512, help="--workload sweep: largest mesh")
     ap.add_argument("--sweep-tol", type=float, default=5e-2,
                     help="--workload sweep: tolerance of the hyperparameter and alpha parts (mesh: 1e-3)")

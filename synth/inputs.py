@@ -5,8 +5,8 @@ He & Mang (arXiv 2510.08782, Sec. 2 and Sec. 3): template/reference images m0, m
 (or densities pi0, pi1) on the periodic box [0, 2*pi)^d and smooth velocity fields.
 It deliberately holds none of the method's arithmetic: no semi-Lagrangian step,
 no cubic interpolation, no spectral differential operator, no objective or gradient.
-Images are analytic Gaussian mixtures, so a warped reference is an exact evaluation
-of the same analytic function at displaced centres; velocities are band-limited random
+Images are analytic Gaussian mixtures or trigonometric polynomials, so a warped reference is an
+exact evaluation of the same analytic function at displaced centres or points; velocities are band-limited random
 Fourier series (synthesised with a plain inverse FFT, a library primitive).
 
 Layout convention (shared by every consumer): a scalar field has shape n = (n_1,...,n_d)
@@ -207,6 +207,39 @@ def blob_image_pair(n, v_true, count, sigma_vox, rng, amplitude_sign=False, norm
     return m0, m1
 
 
+def sinusoid_image_pair(n, v_true, kmax, rng):
+    """Template/reference images from a smooth trigonometric polynomial (the sinusoidal data of the
+    incompressible experiments, Sec. 3.6).
+
+    m(x) = sum over integer k with 0 < |k| <= kmax of a_k cos(k . x) + b_k sin(k . x), a_k, b_k ~ N(0,1).
+    The template is m on the grid; the reference is the same analytic m evaluated at the grid points
+    displaced by v_true (unit time, one explicit step back along the flow: m1(x) = m(x - v_true(x))).
+    Both are mapped by the template's affine min-max map to [0, 1].
+    """
+    n = tuple(int(x) for x in n)
+    d = len(n)
+    rng_k = range(-kmax, kmax + 1)
+    ks = np.array([k for k in np.ndindex(*(len(rng_k),) * d)]) - kmax
+    ks = ks[(np.sum(ks * ks, axis=1) > 0) & (np.sum(ks * ks, axis=1) <= kmax * kmax)]
+    a = rng.standard_normal(len(ks))
+    b = rng.standard_normal(len(ks))
+    grids = np.meshgrid(*coords(n), indexing="ij")
+    pts = np.stack([g.ravel() for g in grids], axis=1)
+
+    def evaluate(points):
+        out = np.zeros(points.shape[0])
+        for start in range(0, len(ks), 32):  # modest temporaries
+            ph = points @ ks[start:start + 32].T.astype(np.float64)
+            out += np.cos(ph) @ a[start:start + 32] + np.sin(ph) @ b[start:start + 32]
+        return out.reshape(n)
+
+    m0 = evaluate(pts)
+    disp = np.stack([v_true[c].ravel() for c in range(d)], axis=1)
+    m1 = evaluate(pts - disp)
+    lo, hi = m0.min(), m0.max()
+    return (m0 - lo) / (hi - lo), (m1 - lo) / (hi - lo)
+
+
 def density_pair(n, v_true, count, sigma_vox, rng, floor=1e-3):
     """Probability densities pi0, pi1 from anisotropic Gaussians (mass-preserving model).
 
@@ -249,6 +282,8 @@ def workload(name, seed=0, n=None):
           'adv3d64'   3D 64^3 advection, low-pass template, |k|<=4 velocity of 2 voxels, nt=4, H2, alpha=1e-3, w=5
           'inc3d128'  3D 128^3 incompressible, nt=8, H1, alpha=1e-2
           'cont3d256' 3D 256^3 mass-preserving (continuity), nt=16, H1, alpha=1e-3, w=10, checkpoint every 4
+          'inc2d256'  2D 256^2 incompressible, sinusoidal images, divergence-free velocity of 4 px, nt=16, H3,
+                      alpha=1e-4, tolerance 1e-3
           'batch'     see batch_workloads()
     n overrides the grid (same recipe at another size, used for small test cases).
     Returns a dict with float64 arrays and the problem/solver settings.
@@ -276,6 +311,13 @@ def workload(name, seed=0, n=None):
         m0, m1 = blob_image_pair(n, v_true, 256, (2.0 * s, 3.0 * s), rng, amplitude_sign=True)
         return dict(name=name, dim=3, n=n, nt=8, model="incompressible", reg_order=1, alpha=1e-2,
                     window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2, ckpt_every=0,
+                    m0=m0, m1=m1, v_true=v_true)
+    if name == "inc2d256":  # the incompressible experiments of Sec. 3.6
+        n = tuple(n or (256, 256))
+        v_true = smooth_velocity(n, 4, 4.0, rng, divergence_free=True)
+        m0, m1 = sinusoid_image_pair(n, v_true, 6, rng)
+        return dict(name=name, dim=len(n), n=n, nt=16, model="incompressible", reg_order=3, alpha=1e-4,
+                    window=10, sigma=4, tau=2, max_iter=200, rel_tol=1e-3, ckpt_every=0,
                     m0=m0, m1=m1, v_true=v_true)
     if name == "cont3d256":
         n = tuple(n or (256, 256, 256))

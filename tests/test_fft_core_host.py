@@ -1,4 +1,4 @@
-"""CPU check of the CUDA library's Stockham FFT core: the radix-2/3/4/5/8 butterflies and stage
+"""CPU check of the CUDA library's Stockham FFT core: the radix-2/3/4/5/8/16 butterflies and stage
 indexing of fft_core.cuh, compiled as host C++ (g++), against a direct long-double DFT."""
 import os
 import shutil
