@@ -143,3 +143,64 @@ def test_point_restricted_steps_equal_the_full_grid():
         xp = departure_points_at(v, 4, -1, pts)
         fulla = adjoint_states(model, m, v, 4, mu=mu)[3]
         np.testing.assert_allclose(adjoint_step_at(model, m, mu, xp, pts, 4), fulla[tuple(pts)], atol=1e-13)
+
+
+# A flow with non-constant velocity whose characteristics are known in closed form (Sec. 2.2, the RK2
+# characteristics): v = (a, b sin x_0) on a 2D periodic grid. Backward along v for a time h_t the
+# departure point is x_0 - a h_t, x_1 - (b/a)(cos(x_0 - a h_t) - cos x_0); forward (the adjoint's
+# characteristics of -v) it is x_0 + a h_t, x_1 + (b/a)(cos x_0 - cos(x_0 + a h_t)). With a = pi/2 on
+# 256 cells, a h_t is a whole number of cells for n_t | 64, so I[v](X*) carries no interpolation error
+# (v_1 depends on x_0 only) and the measured error is the time discretisation alone: one Heun step is
+# the trapezoidal rule for the x_1 integral, local error O(h_t^3); forward Euler, or a predictor
+# X* taken with the wrong sign, is O(h_t^2).
+_RK2_N, _RK2_A, _RK2_B = (256, 8), np.pi / 2, 0.7
+
+
+def _rk2_flow():
+    X = _grid(_RK2_N)
+    return X, np.stack([np.full(_RK2_N, _RK2_A), _RK2_B * np.sin(X[0])])
+
+
+def _rk2_step_errors(sign):
+    from oracle.transport import departure_points
+
+    X, v = _rk2_flow()
+    h = [2 * np.pi / k for k in _RK2_N]
+    errs = []
+    for nt in (4, 8, 16, 32):
+        ht = 1.0 / nt
+        xi = departure_points(v, nt, sign)
+        a, b = _RK2_A, _RK2_B
+        ex0 = X[0] - sign * a * ht
+        ex1 = X[1] - (b / a) * (np.cos(X[0] - sign * a * ht) - np.cos(X[0]))
+        errs.append(max(np.abs(xi[0] * h[0] - ex0).max(), np.abs(xi[1] * h[1] - ex1).max()))
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_rk2_departure_points_third_order_on_closed_form_flow(sign):
+    errs = _rk2_step_errors(sign)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert errs[0] < 5e-3, errs
+    assert np.all(rates > 2.8) and np.all(rates < 3.2), (errs, rates)
+
+
+@pytest.mark.parametrize("bad", ["euler", "predictor_sign"])
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_rk2_pin_catches_planted_mistakes(monkeypatch, bad, sign):
+    """The rate pin above fails for planted mistakes in the oracle's characteristics: a predictor
+    value taken at x (forward Euler) or at the mirrored point x + sign h_t v (predictor sign slip)."""
+    import oracle.transport as tr
+    from oracle.interp import interp as true_interp
+
+    pts = tr.grid_index(_RK2_N)
+
+    def planted(f, xi):
+        if bad == "euler":
+            return true_interp(f, pts)
+        return true_interp(f, 2 * pts - xi)
+
+    monkeypatch.setattr(tr, "interp", planted)
+    errs = _rk2_step_errors(sign)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(rates < 2.3), (errs, rates)
