@@ -120,7 +120,9 @@ long long ga_kernel_launches(void);
  *   out     DEVICE array of count doubles, written in stream order.
  *   stream  cudaStream_t (NULL = legacy default stream); the call returns without synchronising.
  * The first call on a device looks up the device address of the fixed array (cudaGetSymbolAddress);
- * make that first call before any stream capture. Every call on a device shares the array and it
+ * make that first call before any stream capture. The address is kept for the life of the process: a
+ * device reset (cudaDeviceReset, or anything else that destroys the device's primary context) frees
+ * the array, and the entry point must not be called on that device afterwards. Every call on a device shares the array and it
  * keeps the last call's contents (each call rewrites every partial it reads, so nothing needs
  * clearing); calls whose work overlaps on the GPU, e.g. on two streams at once, race on the array
  * and must be serialised by the caller. Errors: GA_ERR_ARG for null pointers, len 0, an unknown

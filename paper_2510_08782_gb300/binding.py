@@ -159,6 +159,56 @@ def _ptrs(dtype, *arrays):
     return [p for p, _ in out], kinds.pop()
 
 
+# Grid of every live context created through this module (handle -> (dim, shape, nt, device index)).
+# The C calls take plain pointers and read as many elements as the context's grid implies, so the
+# wrappers check element counts and devices here: a short array would otherwise be read or written
+# past its end.
+_CTX_INFO = {}
+
+
+def _numel(x):
+    return int(x.numel()) if _is_torch(x) else int(np.asarray(x).size)
+
+
+def _device_of(x):
+    return x.device.index if (_is_torch(x) and x.is_cuda) else None
+
+
+def _check_device(arrays, want=None):
+    """All CUDA tensors of one call on one device, which must be the current device (and the
+    context's device when `want` is given)."""
+    devs = {_device_of(a) for a in arrays} - {None}
+    if not devs:
+        return
+    if len(devs) != 1:
+        raise GaError(1, f"all CUDA tensors of one call must be on one device, got {sorted(devs)}")
+    import torch
+
+    dev = devs.pop()
+    if dev != torch.cuda.current_device():
+        raise GaError(1, f"tensors are on cuda:{dev} but the current device is cuda:{torch.cuda.current_device()}")
+    if want is not None and dev != want:
+        raise GaError(1, f"tensors are on cuda:{dev} but the context lives on cuda:{want}")
+
+
+def _sizes(ctx, **kinds):
+    """Check each array against the context's grid. kinds: name=(array, kind) with kind one of
+    'scalar' (prod n), 'vec' (dim prod n), 'states' ((n_t+1) prod n) or 'half' (2 x the half
+    spectrum: interleaved re, im)."""
+    info = _CTX_INFO.get(ctx)
+    if info is None:
+        return
+    dim, shape, nt, dev = info
+    n = int(np.prod(shape))
+    half = int(np.prod(shape[:-1])) * (shape[-1] // 2 + 1) * 2
+    want = {"scalar": n, "vec": dim * n, "states": (nt + 1) * n, "half": half}
+    for name, (arr, kind) in kinds.items():
+        got = _numel(arr)
+        if got != want[kind]:
+            raise GaError(1, f"{name}: expected {want[kind]} elements for grid {shape} ({kind}), got {got}")
+    _check_device([a for a, _ in kinds.values()], dev)
+
+
 def _current_stream():
     try:
         import torch
@@ -176,18 +226,34 @@ def ga_setup(desc, opts, m0, m1, stream=None):
     """Create a context; returns (handle, element dtype)."""
     dtype = np.float64 if desc.prec == GA_PREC_FP64 else np.float32
     (p0, p1), mem = _ptrs(dtype, m0, m1)
+    shape = tuple(int(desc.n[i]) for i in range(desc.dim))
+    n = int(np.prod(shape)) if desc.dim > 0 else 0
+    if _numel(m0) != n or _numel(m1) != n:
+        raise GaError(1, f"m0, m1: expected {n} elements for grid {shape}, got {_numel(m0)}, {_numel(m1)}")
+    _check_device([m0, m1])
     h = _vp()
     st = lib().ga_setup(ctypes.byref(desc), ctypes.byref(opts), p0, p1, mem,
                         _vp(stream if stream is not None else _current_stream()), ctypes.byref(h))
     _check(st, None)
+    dev = None
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            dev = torch.cuda.current_device()
+    except Exception:
+        pass
+    _CTX_INFO[h.value] = (int(desc.dim), shape, int(desc.nt), dev)
     return h.value
 
 
 def ga_destroy(ctx):
+    _CTX_INFO.pop(ctx, None)
     lib().ga_destroy(ctx)
 
 
 def ga_objective(ctx, dtype, v):
+    _sizes(ctx, v=(v, 'vec'))
     (pv,), mem = _ptrs(dtype, v)
     out = _c_double()
     _check(lib().ga_objective(ctx, pv, mem, ctypes.byref(out)), ctx)
@@ -195,6 +261,7 @@ def ga_objective(ctx, dtype, v):
 
 
 def ga_gradient(ctx, dtype, v, g):
+    _sizes(ctx, v=(v, 'vec'), g=(g, 'vec'))
     (pv, pg), mem = _ptrs(dtype, v, g)
     out = _c_double()
     _check(lib().ga_gradient(ctx, pv, pg, mem, ctypes.byref(out)), ctx)
@@ -202,16 +269,19 @@ def ga_gradient(ctx, dtype, v, g):
 
 
 def ga_deformation(ctx, dtype, v, u, detj):
+    _sizes(ctx, v=(v, 'vec'), u=(u, 'vec'), detj=(detj, 'scalar'))
     (pv, pu, pj), mem = _ptrs(dtype, v, u, detj)
     _check(lib().ga_deformation(ctx, pv, pu, pj, mem), ctx)
 
 
 def ga_precond(ctx, dtype, g, s):
+    _sizes(ctx, g=(g, 'vec'), s=(s, 'vec'))
     (pg, ps), mem = _ptrs(dtype, g, s)
     _check(lib().ga_precond(ctx, pg, ps, mem), ctx)
 
 
 def ga_step(ctx, dtype, v):
+    _sizes(ctx, v=(v, 'vec'))
     (pv,), mem = _ptrs(dtype, v)
     stt = Stats()
     st = lib().ga_step(ctx, pv, mem, ctypes.byref(stt))
@@ -226,6 +296,7 @@ def ga_get_stats(ctx):
 
 
 def ga_solve(ctx, dtype, v):
+    _sizes(ctx, v=(v, 'vec'))
     (pv,), mem = _ptrs(dtype, v)
     stt = Stats()
     st = lib().ga_solve(ctx, pv, mem, ctypes.byref(stt))
@@ -234,6 +305,10 @@ def ga_solve(ctx, dtype, v):
 
 
 def ga_solve_batch(ctxs, dtype, vs):
+    if len(ctxs) != len(vs):
+        raise GaError(1, f"{len(ctxs)} contexts but {len(vs)} velocity arrays")
+    for c, v in zip(ctxs, vs):
+        _sizes(c, v=(v, 'vec'))
     ptrs, mem = _ptrs(dtype, *vs)
     n = len(ctxs)
     carr = (_vp * n)(*ctxs)
@@ -249,21 +324,25 @@ def ga_reset(ctx):
 
 
 def ga_transport(ctx, dtype, v, m1_out):
+    _sizes(ctx, v=(v, 'vec'), m1_out=(m1_out, 'scalar'))
     (pv, pm), mem = _ptrs(dtype, v, m1_out)
     _check(lib().ga_transport(ctx, pv, pm, mem), ctx)
 
 
 def ga_transport_vjp(ctx, dtype, v, gamma, grad_v):
+    _sizes(ctx, v=(v, 'vec'), gamma=(gamma, 'scalar'), grad_v=(grad_v, 'vec'))
     (pv, pgam, pg), mem = _ptrs(dtype, v, gamma, grad_v)
     _check(lib().ga_transport_vjp(ctx, pv, pgam, pg, mem), ctx)
 
 
 def ga_transport_vjp_exact(ctx, dtype, v, gamma, grad_v):
+    _sizes(ctx, v=(v, 'vec'), gamma=(gamma, 'scalar'), grad_v=(grad_v, 'vec'))
     (pv, pgam, pg), mem = _ptrs(dtype, v, gamma, grad_v)
     _check(lib().ga_transport_vjp_exact(ctx, pv, pgam, pg, mem), ctx)
 
 
 def ga_gradient_dto(ctx, dtype, v, g):
+    _sizes(ctx, v=(v, 'vec'), g=(g, 'vec'))
     (pv, pg), mem = _ptrs(dtype, v, g)
     out = _c_double()
     _check(lib().ga_gradient_dto(ctx, pv, pg, mem, ctypes.byref(out)), ctx)
@@ -278,22 +357,27 @@ def _dev(dtype, *arrays):
 
 
 def ga_op_departure(ctx, dtype, v, xm, xp):
+    _sizes(ctx, v=(v, 'vec'), xm=(xm, 'vec'), xp=(xp, 'vec'))
     _check(lib().ga_op_departure(ctx, *_dev(dtype, v, xm, xp)), ctx)
 
 
 def ga_op_forward(ctx, dtype, v, states):
+    _sizes(ctx, v=(v, 'vec'), states=(states, 'states'))
     _check(lib().ga_op_forward(ctx, *_dev(dtype, v, states)), ctx)
 
 
 def ga_op_adjoint(ctx, dtype, v, lam1, lams):
+    _sizes(ctx, v=(v, 'vec'), lam1=(lam1, 'scalar'), lams=(lams, 'states'))
     _check(lib().ga_op_adjoint(ctx, *_dev(dtype, v, lam1, lams)), ctx)
 
 
 def ga_op_body_force(ctx, dtype, v, lam1, b):
+    _sizes(ctx, v=(v, 'vec'), lam1=(lam1, 'scalar'), b=(b, 'vec'))
     _check(lib().ga_op_body_force(ctx, *_dev(dtype, v, lam1, b)), ctx)
 
 
 def ga_op_deriv(ctx, dtype, f, axis, df):
+    _sizes(ctx, f=(f, 'scalar'), df=(df, 'scalar'))
     pf, pd = _dev(dtype, f, df)
     _check(lib().ga_op_deriv(ctx, pf, int(axis), pd), ctx)
 
@@ -312,26 +396,42 @@ def ga_op_set_tiles(ctx, pencils):
 
 
 def ga_op_div(ctx, dtype, v, mu):
+    _sizes(ctx, v=(v, 'vec'), mu=(mu, 'scalar'))
     _check(lib().ga_op_div(ctx, *_dev(dtype, v, mu)), ctx)
 
 
 def ga_op_fft_r2c(ctx, dtype, f, fhat):
+    _sizes(ctx, f=(f, 'scalar'), fhat=(fhat, 'half'))
     _check(lib().ga_op_fft_r2c(ctx, *_dev(dtype, f, fhat)), ctx)
 
 
 def ga_op_fft_c2r(ctx, dtype, fhat, f):
+    _sizes(ctx, fhat=(fhat, 'half'), f=(f, 'scalar'))
     _check(lib().ga_op_fft_c2r(ctx, *_dev(dtype, fhat, f)), ctx)
 
 
 def ga_op_apply_L(ctx, dtype, v, Lv):
+    _sizes(ctx, v=(v, 'vec'), Lv=(Lv, 'vec'))
     _check(lib().ga_op_apply_L(ctx, *_dev(dtype, v, Lv)), ctx)
 
 
 def ga_op_leray(ctx, dtype, v, pv):
+    _sizes(ctx, v=(v, 'vec'), pv=(pv, 'vec'))
     _check(lib().ga_op_leray(ctx, *_dev(dtype, v, pv)), ctx)
 
 
+def _dots_args(a, bs):
+    if len(bs) < 1:
+        raise GaError(1, "at least one vector b_i")
+    na = _numel(a)
+    for i, b in enumerate(bs):
+        if _numel(b) != na:
+            raise GaError(1, f"b[{i}] has {_numel(b)} elements, a has {na}")
+
+
 def ga_op_dots(ctx, dtype, a, bs):
+    _dots_args(a, bs)
+    _check_device([a, *bs], (_CTX_INFO.get(ctx) or (None,) * 4)[3])
     ptrs = _dev(dtype, a, *bs)
     n = len(bs)
     arr = (_vp * n)(*ptrs[1:])
@@ -355,12 +455,16 @@ def ga_dots_noalloc(dtype, a, bs, out, stream=None):
     """FP64-accurate inner products <a, b_i> into the device array `out` (float64, len(bs)) without
     any device allocation; see include/ga_ops.h for who needs this and its limits (at most 32 vectors,
     calls that overlap on the GPU race)."""
+    _dots_args(a, bs)
     ptrs = _dev(dtype, a, *bs)
     (pout,) = _dev(np.float64, out)
     n = len(bs)
+    if _numel(out) < n:
+        raise GaError(1, f"out holds {_numel(out)} doubles, {n} are written")
+    _check_device([a, *bs, out])
     arr = (_vp * n)(*ptrs[1:])
     prec = GA_PREC_FP64 if dtype == np.float64 else GA_PREC_MIXED
-    st = lib().ga_dots_noalloc(prec, ptrs[0], arr, n, int(np.prod(tuple(a.shape))), pout,
+    st = lib().ga_dots_noalloc(prec, ptrs[0], arr, n, _numel(a), pout,
                                _vp(stream if stream is not None else _current_stream()))
     _check(st, None)
 

@@ -33,7 +33,9 @@ double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once per device. In host
 // code `g_dot_scratch` names a host-side stand-in, never the device array, so it must not be passed
-// to a kernel.
+// to a kernel. A device reset (cudaDeviceReset, or anything else that destroys the device's primary
+// context) unloads the module and frees the array, so the cached address then points at freed
+// memory: the entry point must not be called on that device again in the same process.
 cudaError_t scratch_for_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

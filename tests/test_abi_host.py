@@ -121,3 +121,29 @@ def test_binding_rejects_wrong_dtype(libga):
         _ptr(np.zeros(4, dtype=np.float32), np.float64)
     with pytest.raises(GaError):
         _ptr(np.zeros((4, 4))[:, ::2], np.float64)
+
+
+def test_binding_rejects_arrays_that_do_not_match_the_context_grid(libga):
+    """The C calls read and write as many elements as the context's grid implies; the binding refuses
+    a short or long array (or a short pointer list or output for the inner products) before any call
+    reaches the library."""
+    b = libga
+    fake = 0x1234  # a registered grid only: every check below raises before the C call
+    b._CTX_INFO[fake] = (3, (4, 6, 8), 2, None)
+    try:
+        n = 4 * 6 * 8
+        vec, short = np.zeros(3 * n, np.float32), np.zeros(3 * n - 1, np.float32)
+        with pytest.raises(b.GaError, match="elements"):
+            b.ga_op_departure(fake, np.float32, vec, short, vec)
+        with pytest.raises(b.GaError, match="elements"):
+            b.ga_op_forward(fake, np.float32, vec, np.zeros(2 * n, np.float32))  # needs (n_t + 1) n
+        with pytest.raises(b.GaError, match="elements"):
+            b.ga_op_fft_r2c(fake, np.float32, np.zeros(n, np.float32), np.zeros(n, np.float32))
+        with pytest.raises(b.GaError, match="elements"):
+            b.ga_gradient(fake, np.float32, vec, short)
+        with pytest.raises(b.GaError, match="b\\[1\\]"):
+            b.ga_op_dots(fake, np.float32, vec, [vec, short])
+    finally:
+        b._CTX_INFO.pop(fake, None)
+    with pytest.raises(b.GaError, match="b\\[0\\]"):
+        b.ga_dots_noalloc(np.float32, np.zeros(8, np.float32), [np.zeros(7, np.float32)], np.zeros(1))

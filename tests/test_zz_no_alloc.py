@@ -26,8 +26,9 @@ def _lib():
     build.build()
 
 
+@pytest.mark.parametrize("count", [1, 6, 17, 32])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_noalloc_dots_match_context_dots_on_two_calls(prec):
+def test_noalloc_dots_match_context_dots_on_two_calls(prec, count):
     import torch
 
     import paper_2510_08782_gb300 as ga
@@ -43,15 +44,23 @@ def test_noalloc_dots_match_context_dots_on_two_calls(prec):
     code = ga.GA_PREC_FP64 if prec == "fp64" else ga.GA_PREC_MIXED
     n = 3 * int(np.prod(shape))
     for _ in range(2):  # two calls in a row: the fixed scratch array keeps the previous call's data
-        vecs = [torch.from_numpy(rng.standard_normal(n)).to(tdtype).cuda() for _ in range(6)]
-        ref = ga.ga_op_dots(P.ctx, P.dtype, vecs[0], vecs)
-        out = torch.full((6,), float("nan"), dtype=torch.float64, device="cuda")
-        ptrs = (ctypes.c_void_p * 6)(*[v.data_ptr() for v in vecs])
-        st = L.ga_dots_noalloc(code, vecs[0].data_ptr(), ptrs, 6, n, out.data_ptr(), None)
+        host = [rng.standard_normal(n).astype(dtype) for _ in range(count)]
+        vecs = [torch.from_numpy(x).cuda() for x in host]
+        a = vecs[0]
+        ref = ga.ga_op_dots(P.ctx, P.dtype, a, vecs)
+        out = torch.full((count,), float("nan"), dtype=torch.float64, device="cuda")
+        ptrs = (ctypes.c_void_p * count)(*[v.data_ptr() for v in vecs])
+        st = L.ga_dots_noalloc(code, a.data_ptr(), ptrs, count, n, out.data_ptr(), None)
         assert st == 0, ga.ga_last_error(None)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0.0)
+        # and directly against the products summed in FP64 on the host: the inputs are exact in FP64,
+        # so both sides carry only summation error (compensated on the device, pairwise in NumPy)
+        a64 = host[0].astype(np.float64)
+        for i, x in enumerate(host):
+            prods = a64 * x.astype(np.float64)
+            assert abs(got[i] - prods.sum()) <= 64 * 2.3e-16 * np.abs(prods).sum(), i
 
 
 def test_noalloc_dots_refuse_more_vectors_than_the_fixed_array_holds():
