@@ -29,6 +29,8 @@
 #ifndef GA_H
 #define GA_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -41,7 +43,7 @@ typedef enum {
   GA_ERR_NAN = 4,            /* NaN/Inf in the objective or the gradient                 */
   GA_ERR_LINESEARCH = 5,     /* Armijo search exhausted max_backtracks halvings          */
   GA_ERR_NOT_CONVERGED = 6,  /* informational: ga_solve hit max_iter; v and stats valid  */
-  GA_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up                       */
+  GA_ERR_TIMEOUT = 7         /* reserved: no call waits on the device, none returns it   */
 } ga_status;
 
 typedef enum {
@@ -120,9 +122,20 @@ typedef struct ga_ctx ga_ctx; /* opaque; owns all device memory of one problem *
 
 /* Create a context on the current CUDA device. m0, m1: template/reference (or densities pi0,
  * pi1) as scalar fields of the descriptor's element type. stream: a cudaStream_t (NULL = the
- * legacy default stream) on which all work of this context is ordered. */
+ * legacy default stream) on which all work of this context is ordered. Before it allocates
+ * anything, ga_setup compares the workspace (ga_workspace_bytes) with the device's free memory and
+ * returns GA_ERR_NOMEM, with the two figures in the message, when it does not fit; a cudaMalloc that
+ * still fails later (another allocator took the memory meanwhile) also returns GA_ERR_NOMEM. Either
+ * way nothing stays allocated and *out is NULL. */
 ga_status ga_setup(const ga_problem_desc* desc, const ga_solver_opts* opts, const void* m0,
                    const void* m1, int mem, void* stream, ga_ctx** out);
+
+/* Device memory (bytes) that ga_setup allocates for this descriptor and these options: every field,
+ * trajectory slot, spectral work area, window pool and FP64 scratch array of the context, summed as
+ * requested (the allocator rounds each allocation up further). Host arithmetic only: no GPU is
+ * needed. The discretise-then-optimise gradient adds one vector field on its first call.
+ * GA_ERR_ARG for an invalid descriptor or options (the same checks as ga_setup). */
+ga_status ga_workspace_bytes(const ga_problem_desc* desc, const ga_solver_opts* opts, size_t* bytes);
 
 /* obj(v) (Eq. (1a)): one state solve (forward only). */
 ga_status ga_objective(ga_ctx* ctx, const void* v, int mem, double* obj);

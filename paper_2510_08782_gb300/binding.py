@@ -60,6 +60,8 @@ def library_path():
 _LIB = None
 
 _SIGS = {
+    "ga_workspace_bytes": ([ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOpts), ctypes.POINTER(ctypes.c_size_t)],
+                           _c_int),
     "ga_setup": ([ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolverOpts), _vp, _vp, _c_int, _vp,
                   ctypes.POINTER(_vp)], _c_int),
     "ga_objective": ([_vp, _vp, _c_int, ctypes.POINTER(_c_double)], _c_int),
@@ -245,6 +247,13 @@ def ga_setup(desc, opts, m0, m1, stream=None):
         pass
     _CTX_INFO[h.value] = (int(desc.dim), shape, int(desc.nt), dev)
     return h.value
+
+
+def ga_workspace_bytes(desc, opts):
+    """Device bytes ga_setup allocates for this descriptor and these options (host arithmetic)."""
+    out = ctypes.c_size_t()
+    _check(lib().ga_workspace_bytes(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(out)), None)
+    return int(out.value)
 
 
 def ga_destroy(ctx):

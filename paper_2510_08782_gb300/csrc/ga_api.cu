@@ -22,6 +22,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -96,6 +97,7 @@ template <typename T> struct Engine : EngineBase {
   long long nv, vl;
   cudaStream_t st;
   FftTables<T> ft;
+  cx<T>* twd[3] = {nullptr, nullptr, nullptr};  // the device twiddle tables ft.tw points at
   std::vector<void*> allocs;
   void* pinned = nullptr;
   double* hres = nullptr;
@@ -159,10 +161,9 @@ template <typename T> struct Engine : EngineBase {
     return static_cast<U*>(p);
   }
 
-  void init(ga_ctx* c, const void* hm0, const void* hm1, int mem) {
-    ctx = c;
-    st = c->st;
-    const ga_problem_desc& d = c->desc;
+  // Sizes that follow from the descriptor and the solver options (shared by init and the workspace
+  // planner, ga_workspace_bytes).
+  void derive(const ga_problem_desc& d, const ga_solver_opts& o) {
     dim = d.dim;
     nt = d.nt;
     model = d.model;
@@ -187,8 +188,75 @@ template <typename T> struct Engine : EngineBase {
     ht = 1.0 / nt;
     hd = 1.0;
     for (int a = 3 - dim; a < 3; ++a) hd *= 2.0 * M_PI / g.n[a];
+    nslots = (K == 0) ? nt : (nt / K + (nt % K != 0 ? 1 : 0));
+    // solver pools: window (w+1) + trial q + one more, for iterates and gradients. An iterate buffer
+    // holds v in [0, vl) and w = alpha L v in [vl, 2 vl); S holds s and alpha L s the same way.
+    W1 = o.window + 1;
+    resident = o.graphs == 2;
+    graphs = o.graphs == 1;
+  }
+
+  // Every device buffer a context holds from ga_setup on, in allocation order: al(pointer, element
+  // count). The only later allocation is the discretise-then-optimise gradient's buffer (one vector
+  // field, on its first use).
+  template <class A> void layout(A&& al) {
+    for (int a = 0; a < 3; ++a) al(twd[a], (long long)g.n[a]);  // twiddle tables exp(-2 pi i m / n_a)
+    al(m0, nv);
+    al(m1, nv);
+    al(xm, vl);
+    al(xp, vl);
+    al(mu, nv);
+    al(lam[0], nv);
+    al(lam[1], nv);
+    al(tmp[0], nv);
+    al(tmp[1], nv);
+    al(body, vl);
+    al(io_a, vl);
+    al(io_b, vl);
+    al(states, (long long)nslots * nv);
+    if (K > 1) al(seg, (long long)(K - 1) * nv);
+    al(vh, g.nhalf * dim);
+    al(bh, g.nhalf * dim);
+    al(dpart, (long long)kMaxDots * kRedBlocks);
+    al(dres, (long long)kNumRes);
+    if (resident) {  // the same memory as the pools, in fixed roles (see the device-driven solve below)
+      al(VC, 2 * vl);
+      al(Q, 2 * vl);
+      al(GC, vl);
+      al(GQ, vl);
+      al(RV, (long long)W1 * 2 * vl);
+      al(RG, (long long)W1 * vl);
+      al(dctl, 1LL);
+    } else {
+      for (int i = 0; i < W1 + 2; ++i) {
+        T* pv = nullptr;
+        T* pg = nullptr;
+        al(pv, 2 * vl);
+        al(pg, vl);
+        vfree.push_back(pv);
+        gfree.push_back(pg);
+      }
+    }
+    al(S, 2 * vl);
+    al(wtmp, vl);
+    if (graphs) {
+      al(gin, 2 * vl);
+      al(gbuf, vl);
+    }
+    al(dM, (long long)W1 * W1);
+    al(dbeta, (long long)kMaxWin + 4);
+  }
+
+  void init(ga_ctx* c, const void* hm0, const void* hm1, int mem) {
+    ctx = c;
+    st = c->st;
+    derive(c->desc, c->opts);
     ck(cudaEventCreate(&ev[0]), "cudaEventCreate");
     ck(cudaEventCreate(&ev[1]), "cudaEventCreate");
+    layout([&](auto*& p, long long count) {
+      using U = std::remove_reference_t<decltype(*p)>;
+      p = dalloc<U>(count);
+    });
 
     // FFT plans and twiddle tables per internal axis
     for (int a = 0; a < 3; ++a) {
@@ -200,70 +268,24 @@ template <typename T> struct Engine : EngineBase {
         const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m / L;
         tw[m] = mk<T>((T)cosl(ang), (T)sinl(ang));
       }
-      cx<T>* dtw = dalloc<cx<T>>(L);
-      ck(cudaMemcpy(dtw, tw.data(), sizeof(cx<T>) * L, cudaMemcpyHostToDevice), "twiddle upload");
-      ft.tw[a] = dtw;
+      ck(cudaMemcpy(twd[a], tw.data(), sizeof(cx<T>) * L, cudaMemcpyHostToDevice), "twiddle upload");
+      ft.tw[a] = twd[a];
     }
 
-    m0 = dalloc<T>(nv);
-    m1 = dalloc<T>(nv);
     const cudaMemcpyKind kind = mem == GA_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     ck(cudaMemcpyAsync(m0, hm0, sizeof(T) * nv, kind, st), "copy m0");
     ck(cudaMemcpyAsync(m1, hm1, sizeof(T) * nv, kind, st), "copy m1");
-    xm = dalloc<T>(vl);
-    xp = dalloc<T>(vl);
-    mu = dalloc<T>(nv);
-    lam[0] = dalloc<T>(nv);
-    lam[1] = dalloc<T>(nv);
-    tmp[0] = dalloc<T>(nv);
-    tmp[1] = dalloc<T>(nv);
-    body = dalloc<T>(vl);
-    io_a = dalloc<T>(vl);
-    io_b = dalloc<T>(vl);
-    nslots = (K == 0) ? nt : (nt / K + (nt % K != 0 ? 1 : 0));
-    states = dalloc<T>((long long)nslots * nv);
-    if (K > 1) seg = dalloc<T>((long long)(K - 1) * nv);
-    vh = dalloc<cx<T>>(g.nhalf * dim);
-    bh = dalloc<cx<T>>(g.nhalf * dim);
-    dpart = dalloc<double>((long long)kMaxDots * kRedBlocks);
-    dres = dalloc<double>(kNumRes);
     ck(cudaMallocHost(&pinned, sizeof(double) * kNumRes), "cudaMallocHost");
     hres = static_cast<double*>(pinned);
-
-    // solver pools: window (w+1) + trial q + one more, for iterates and gradients. An iterate buffer
-    // holds v in [0, vl) and w = alpha L v in [vl, 2 vl); S holds s and alpha L s the same way.
-    W1 = c->opts.window + 1;
-    resident = c->opts.graphs == 2;
-    if (resident) {  // the same memory as the pools, in fixed roles (see the device-driven solve below)
-      VC = dalloc<T>(2 * vl);
-      Q = dalloc<T>(2 * vl);
-      GC = dalloc<T>(vl);
-      GQ = dalloc<T>(vl);
-      RV = dalloc<T>((long long)W1 * 2 * vl);
-      RG = dalloc<T>((long long)W1 * vl);
-      dctl = dalloc<ResCtl>(1);
+    if (resident) {
       void* hp = nullptr;
       ck(cudaMallocHost(&hp, sizeof(ResCtl)), "cudaMallocHost");
       hctl = static_cast<ResCtl*>(hp);
       std::memset(hctl, 0, sizeof(ResCtl));
       for (auto& cs : cap) ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
-    } else {
-      for (int i = 0; i < W1 + 2; ++i) {
-        vfree.push_back(dalloc<T>(2 * vl));
-        gfree.push_back(dalloc<T>(vl));
-      }
     }
-    S = dalloc<T>(2 * vl);
-    wtmp = dalloc<T>(vl);
-    graphs = c->opts.graphs == 1;
-    if (graphs) {
-      gin = dalloc<T>(2 * vl);
-      gbuf = dalloc<T>(vl);
-      if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
-        ck(cudaStreamCreate(&gst), "capture stream");
-    }
-    dM = dalloc<double>((long long)W1 * W1);
-    dbeta = dalloc<double>(kMaxWin + 4);
+    if (graphs && (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread))
+      ck(cudaStreamCreate(&gst), "capture stream");
     ck(cudaMemsetAsync(dM, 0, sizeof(double) * W1 * W1, st), "memset");
     autotune_tiles();
     ck(cudaStreamSynchronize(st), "setup sync");
@@ -1389,6 +1411,34 @@ namespace ga {
 void set_global_error(const char* msg) { g_setup_err = msg ? msg : ""; }
 }  // namespace ga
 
+static bool valid_setup(const ga_problem_desc& d, const ga_solver_opts& o) {
+  bool ok = (d.dim == 2 || d.dim == 3) && d.nt >= 1 && d.nt <= 4096 && d.model >= 0 && d.model <= 2 &&
+            d.reg_order >= 1 && d.reg_order <= 3 && d.alpha > 0.0 && std::isfinite(d.alpha) &&
+            (d.prec == GA_PREC_FP64 || d.prec == GA_PREC_MIXED) && d.ckpt_every >= 0;
+  for (int a = 0; ok && a < d.dim; ++a) ok = good_len(d.n[a]);
+  return ok && o.window >= 0 && o.window < kMaxWin && o.window + 2 <= kMaxDots && o.sigma >= 1 && o.tau >= 0 &&
+         o.max_iter >= 1 && o.rel_tol >= 0.0 && o.armijo_c > 0.0 && o.max_backtracks >= 0 &&
+         o.max_backtracks <= 200 && (o.variant == 1 || o.variant == 2) &&
+         (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD || o.method == GA_METHOD_GA_AA) &&
+         (o.graphs == 0 || o.graphs == 1 || (o.graphs == 2 && o.method != GA_METHOD_GA_AA));
+}
+
+// Bytes of the buffers ga_setup allocates on the device, from the same layout the engine allocates.
+template <typename T> static size_t planned_bytes(const ga_problem_desc& d, const ga_solver_opts& o) {
+  auto e = std::make_unique<Engine<T>>();
+  e->derive(d, o);
+  size_t b = 0;
+  e->layout([&](auto*& p, long long count) {
+    using U = std::remove_reference_t<decltype(*p)>;
+    b += sizeof(U) * (size_t)std::max(count, 1LL);
+  });
+  return b;
+}
+
+static size_t planned_bytes(const ga_problem_desc& d, const ga_solver_opts& o) {
+  return d.prec == GA_PREC_MIXED ? planned_bytes<float>(d, o) : planned_bytes<double>(d, o);
+}
+
 extern "C" {
 
 const char* ga_status_str(ga_status s) {
@@ -1411,6 +1461,16 @@ const char* ga_last_error(const ga_ctx* ctx) {
   return g_setup_err.empty() ? "null context" : g_setup_err.c_str();
 }
 
+ga_status ga_workspace_bytes(const ga_problem_desc* desc, const ga_solver_opts* opts, size_t* bytes) {
+  if (!desc || !opts || !bytes) return GA_ERR_ARG;
+  if (!valid_setup(*desc, *opts)) {
+    g_setup_err = "invalid problem descriptor or solver options";
+    return GA_ERR_ARG;
+  }
+  *bytes = planned_bytes(*desc, *opts);
+  return GA_OK;
+}
+
 ga_status ga_setup(const ga_problem_desc* desc, const ga_solver_opts* opts, const void* m0, const void* m1,
                    int mem, void* stream, ga_ctx** out) {
   if (!out) return GA_ERR_ARG;
@@ -1418,19 +1478,26 @@ ga_status ga_setup(const ga_problem_desc* desc, const ga_solver_opts* opts, cons
   if (!desc || !opts || !m0 || !m1) return GA_ERR_ARG;
   const ga_problem_desc& d = *desc;
   const ga_solver_opts& o = *opts;
-  bool ok = (d.dim == 2 || d.dim == 3) && d.nt >= 1 && d.nt <= 4096 && d.model >= 0 && d.model <= 2 &&
-            d.reg_order >= 1 && d.reg_order <= 3 && d.alpha > 0.0 && std::isfinite(d.alpha) &&
-            (d.prec == GA_PREC_FP64 || d.prec == GA_PREC_MIXED) && d.ckpt_every >= 0 &&
-            (mem == GA_MEM_HOST || mem == GA_MEM_DEVICE);
-  for (int a = 0; ok && a < d.dim; ++a) ok = good_len(d.n[a]);
-  ok = ok && o.window >= 0 && o.window < kMaxWin && o.window + 2 <= kMaxDots && o.sigma >= 1 && o.tau >= 0 &&
-       o.max_iter >= 1 && o.rel_tol >= 0.0 && o.armijo_c > 0.0 && o.max_backtracks >= 0 &&
-       o.max_backtracks <= 200 && (o.variant == 1 || o.variant == 2) &&
-       (o.method == GA_METHOD_GA_NGMRES || o.method == GA_METHOD_RPGD || o.method == GA_METHOD_GA_AA) &&
-       (o.graphs == 0 || o.graphs == 1 || (o.graphs == 2 && o.method != GA_METHOD_GA_AA));
-  if (!ok) {
+  if (!valid_setup(d, o) || (mem != GA_MEM_HOST && mem != GA_MEM_DEVICE)) {
     g_setup_err = "invalid problem descriptor or solver options";
     return GA_ERR_ARG;
+  }
+  {  // refuse, before allocating anything, a workspace larger than the device's free memory
+    const size_t need = planned_bytes(d, o);
+    size_t free_b = 0, total_b = 0;
+    const cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g_setup_err = std::string("cudaMemGetInfo: ") + cudaGetErrorString(e);
+      return GA_ERR_CUDA;
+    }
+    if (need > free_b) {
+      char buf[192];
+      std::snprintf(buf, sizeof buf, "the problem needs %zu bytes of device memory, %zu are free (of %zu)", need,
+                    free_b, total_b);
+      g_setup_err = buf;
+      return GA_ERR_NOMEM;
+    }
   }
   ga_ctx* c = new ga_ctx();
   c->desc = d;

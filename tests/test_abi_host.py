@@ -147,3 +147,38 @@ def test_binding_rejects_arrays_that_do_not_match_the_context_grid(libga):
         b._CTX_INFO.pop(fake, None)
     with pytest.raises(b.GaError, match="b\\[0\\]"):
         b.ga_dots_noalloc(np.float32, np.zeros(8, np.float32), [np.zeros(7, np.float32)], np.zeros(1))
+
+
+def _desc_opts(libga, n=(16, 16, 16), prec=1, nt=16, K=0, window=5, graphs=0):
+    d = libga.ProblemDesc()
+    d.dim = len(n)
+    for i, x in enumerate(n):
+        d.n[i] = x
+    d.nt, d.model, d.reg_order, d.alpha, d.prec, d.ckpt_every = nt, 1, 1, 1e-3, prec, K
+    o = libga.SolverOpts()
+    o.window, o.sigma, o.tau, o.max_iter, o.rel_tol = window, 4, 2, 10, 1e-2
+    o.armijo_c, o.max_backtracks, o.variant, o.method, o.graphs = 1e-4, 20, 1, 0, graphs
+    return d, o
+
+
+def test_workspace_planner_follows_the_context_layout(libga):
+    """ga_workspace_bytes is host arithmetic: each part of the context layout changes it by the
+    bytes that part holds."""
+    wb = libga.ga_workspace_bytes
+    n = (16, 16, 16)
+    nv, s = 16 ** 3, 4
+    vl = 3 * nv
+    base = wb(*_desc_opts(libga, n))
+    # one more window slot: one more iterate (v and alpha L v) and gradient, and a larger FP64 Gram
+    w6 = wb(*_desc_opts(libga, n, window=6))
+    assert w6 - base == 3 * vl * s + (7 * 7 - 6 * 6) * 8
+    # checkpoints every 4 of 16 steps: 4 stored states and 3 recompute slots instead of 16 states
+    ck = wb(*_desc_opts(libga, n, K=4))
+    assert base - ck == (16 - 4 - 3) * nv * s
+    # FP64 doubles every field; the FP64 scratch arrays and the Gram do not change
+    d64 = wb(*_desc_opts(libga, n, prec=0))
+    fixed = base - (d64 - base)
+    assert 0 < fixed < 1_000_000
+    # an invalid descriptor is refused like ga_setup refuses it
+    with pytest.raises(libga.GaError):
+        wb(*_desc_opts(libga, (16, 16, 7)))
