@@ -40,7 +40,8 @@ SETTINGS = dict(nt=NT, model="continuity", reg_order=1, alpha=1e-3, ckpt_every=4
                 tau=2, max_iter=200, rel_tol=1e-2)
 WORKLOAD_NAME = ("cont3d256: 256^3 continuity (mass-preserving), nt=16, H1 alpha=1e-3, "
                  "GA-NGMRES(10;4,2), checkpoint every 4, 64 anisotropic Gaussian densities, 6-voxel velocity")
-CPU_SAMPLE_N = 48  # oracle sample grid (same recipe), scaled to 256^3 by voxel count
+CPU_SAMPLE_N = 80  # oracle sample grid of the default line (same recipe), scaled to 256^3 by voxel count
+REF_SAMPLE_N = 48  # oracle sample grid of each step of the reference arm
 
 # kernel classes timed with events inside the library (ga_prof_start)
 PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ, PROF_DERIV_PAIR = 0, 1, 2, 3, 4
@@ -138,38 +139,107 @@ def make_inputs(n=N, seed=0):
     return workload("cont3d256", seed=seed, n=(n, n, n))
 
 
-def cpu_baseline(steps=1, warmup=0, n=CPU_SAMPLE_N):
-    """The FP64 oracle's reduced gradient on an n^3 sample of the same recipe, scaled to 256^3."""
+def _oracle_worker(job):
+    """One host process: the unmodified FP64 oracle on an n^3 sample of the benchmark recipe. Runs
+    `warmup` untimed and `steps` timed evaluations of `kind` ('gradient' or 'objective') at
+    v = v_true / 2 and returns the seconds of each timed evaluation."""
+    n, kind, steps, warmup = job
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
     from oracle.problem import Problem as OProblem
 
     w = make_inputs(n)
     P = OProblem(w["m0"], w["m1"], nt=NT, model="continuity", reg_order=1, alpha=1e-3)
-    v = np.zeros((3, n, n, n))
+    v = 0.5 * w["v_true"]
+    fn = P.gradient if kind == "gradient" else P.objective
     for _ in range(warmup):
-        P.gradient(v)
-    t0 = time.perf_counter()
+        fn(v)
+    out = []
     for _ in range(steps):
-        P.gradient(v)
-    dt = (time.perf_counter() - t0) / steps
+        t0 = time.perf_counter()
+        fn(v)
+        out.append(time.perf_counter() - t0)
+    return out
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_oracle_pool(jobs):
+    """Run oracle jobs in a pool of spawned processes, one per job, all concurrently (the pool is
+    spawned, never forked: the parent may hold a CUDA context). Each child is held to one thread so
+    the processes do not oversubscribe the cores."""
+    import multiprocessing as mp
+
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(len(jobs)) as pool:
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, jobs)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, val in saved.items():
+            if val is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = val
+    return res, wall
+
+
+def cpu_baseline(n=CPU_SAMPLE_N, cores=None):
+    """The FP64 oracle, as it stands (single-threaded NumPy), on every host core at once: each core
+    runs one independent evaluation on an n^3 sample of the same recipe (three quarters of the cores
+    a reduced gradient, the rest an objective). Throughput = gradient evaluations per second of all
+    cores, scaled to 256^3 by the voxel count."""
+    cores = cores or host_cores()
+    n_obj = max(1, cores // 4) if cores > 1 else 0
+    jobs = [(n, "gradient", 1, 0)] * (cores - n_obj) + [(n, "objective", 1, 0)] * n_obj
+    res, wall = run_oracle_pool(jobs)
+    tg = [t for r, j in zip(res, jobs) if j[1] == "gradient" for t in r]
+    to = [t for r, j in zip(res, jobs) if j[1] == "objective" for t in r]
     scale = (N / n) ** 3
-    return {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} FP64 oracle reduced-gradient evaluation(s) of the same recipe at {n}^3 "
-                      f"(nt=16), {dt:.2f} s each, scaled to 256^3 by voxel count x{scale:.0f}; "
-                      "NumPy single-threaded (gathers and pocketfft)"}
+    t_grad = statistics.mean(tg)  # seconds per gradient on one core at n^3
+    t_obj = statistics.mean(to) if to else None
+    value = cores / (t_grad * scale)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} concurrent single-threaded FP64 oracle evaluations of the same recipe at {n}^3 "
+                      f"(nt=16, v = v_true/2): {len(tg)} reduced gradients ({t_grad:.1f} s each) and {len(to)} "
+                      f"objectives; throughput = cores / seconds per gradient, scaled to 256^3 by voxel count "
+                      f"x{scale:.1f}; pool wall {wall:.1f} s",
+            "s_per_grad_1core_256": t_grad * scale,
+            "s_per_obj_1core_256": (t_obj * scale) if t_obj else None}
 
 
 def run_reference(args):
+    """The oracle arm: K timed steps after W warm-ups, each step one reduced gradient per host core at
+    the reference sample size (all cores concurrently), scaled to 256^3 by voxel count."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    cb = cpu_baseline(steps=args.steps, warmup=args.warmup)
-    dt_step = 1.0 / (cb["value"] * (N / CPU_SAMPLE_N) ** 3)
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_step * 1e3, "higher_is_better": True,
+    n = REF_SAMPLE_N
+    cores = host_cores()
+    res, wall = run_oracle_pool([(n, "gradient", args.steps, args.warmup)] * cores)
+    per = [t for r in res for t in r]
+    t_grad = statistics.mean(per)
+    scale = (N / n) ** 3
+    value = cores / (t_grad * scale)
+    sample = (f"each step: {cores} concurrent single-threaded FP64 oracle reduced gradients of the same recipe at "
+              f"{n}^3 (nt=16), {t_grad:.2f} s each, scaled to 256^3 by voxel count x{scale:.0f}; pool wall "
+              f"{wall:.1f} s for {args.warmup} warm-up + {args.steps} timed steps")
+    cb = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_grad * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "sample": cb["sample"]},
+            "config": {"workload": WORKLOAD_NAME, "sample": sample},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -313,15 +383,86 @@ def run_sweep(args):
 GRAPH_MODES = {"off": False, "replay": True, "device": "device"}
 
 
+def _batch_problem_worker(spec):
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    from synth.inputs import batch_problem
+
+    w = batch_problem(spec)
+    return {k: w[k] for k in ("n", "nt", "alpha", "m0", "m1")}
+
+
+def batch_inputs(count=32, seed=0):
+    """The seeded batch of uneven advection problems, generated on all host cores (spawned pool)."""
+    import multiprocessing as mp
+
+    from synth.inputs import batch_specs
+
+    specs = batch_specs(count, seed=seed)
+    with mp.get_context("spawn").Pool(min(len(specs), host_cores())) as pool:
+        return pool.map(_batch_problem_worker, specs)
+
+
+BATCH_NAME = ("batch: 32 independent 3D advection problems, grids drawn from {64,96,128,160}^3 (seeded), nt=4, "
+              "H1, alpha in {1e-2,1e-3}, GA-NGMRES(5;4,2) to rel-grad 1e-2, FP32 fields with FP64 reductions")
+
+
+def measure_batch(probs, graphs, steps, warmup, barrier=None):
+    """Solve the batch with ga_solve_batch `warmup` + `steps` times from v = 0; returns seconds per
+    batch (mean of the timed solves), problems/s and the per-problem statistics of the last solve.
+    graphs: 'off' one host worker and stream per problem; 'device' the whole batch as one CUDA graph
+    launch with the solver's decisions on the device; 'replay' host workers replaying evaluations."""
+    import torch
+
+    import paper_2510_08782_gb300 as ga
+
+    barrier = barrier or torch.cuda.synchronize
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    streams = [torch.cuda.Stream() for _ in probs]
+    ctxs, vs = [], []
+    for w, st in zip(probs, streams):
+        d0, d1 = dev(w["m0"]), dev(w["m1"])
+        torch.cuda.synchronize()  # pooled streams do not order themselves after the default stream
+        ctxs.append(ga.Problem(d0, d1, nt=w["nt"], model="advection", reg_order=1, alpha=w["alpha"],
+                               prec="mixed", window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2,
+                               stream=st.cuda_stream, graphs=GRAPH_MODES[graphs]))
+        vs.append(torch.zeros((3,) + tuple(w["n"]), dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+
+    def solve_all():
+        for v in vs:
+            v.zero_()
+        torch.cuda.synchronize()
+        return ga.ga_solve_batch([P.ctx for P in ctxs], np.float32, vs)
+
+    for _ in range(warmup):
+        solve_all()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        stats, status = solve_all()
+    barrier()
+    dt = time.perf_counter() - t0
+    per = [{"n": int(w["n"][0]), "alpha": w["alpha"], "iters": st.iters, "grad_evals": st.grad_evals,
+            "obj_evals": st.obj_evals, "converged": bool(st.converged), "rel_grad_inf": st.rel_grad_inf}
+           for w, st in zip(probs, stats)]
+    for P in ctxs:
+        P.close()
+    del vs
+    torch.cuda.synchronize()
+    return {"graphs": graphs, "s_per_batch": dt / steps, "problems_per_s": len(probs) * steps / dt,
+            "timed_solves": steps, "warmup_solves": warmup, "iters_total": sum(r["iters"] for r in per),
+            "all_converged": all(r["converged"] for r in per), "per_problem": per}, dt
+
+
 def run_batch(args):
     """Batched form: 32 independent 3D advection problems with grids drawn from {64,96,128,160}^3,
     n_t = 4, H1, alpha in {1e-2, 1e-3}, GA-NGMRES(5; 4, 2) to rel-grad 1e-2, FP32 fields. One step =
-    one ga_solve_batch over all problems (each on its own stream, driven concurrently)."""
+    one ga_solve_batch over all problems."""
     import torch
 
     import paper_2510_08782_gb300 as ga
     from paper_2510_08782_gb300 import build
-    from synth.inputs import batch_workloads
 
     build.build()
     ws, rank, local = dist_env()
@@ -334,42 +475,9 @@ def run_batch(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    probs = batch_workloads(32, seed=rank)
-    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
-    streams = [torch.cuda.Stream() for _ in probs]
-    ctxs, vs = [], []
-    for w, st in zip(probs, streams):
-        d0, d1 = dev(w["m0"]), dev(w["m1"])
-        torch.cuda.synchronize()  # pooled streams do not order themselves after the default stream
-        P = ga.Problem(d0, d1, nt=w["nt"], model="advection", reg_order=1, alpha=w["alpha"],
-                       prec="mixed", window=5, sigma=4, tau=2, max_iter=200, rel_tol=1e-2, stream=st.cuda_stream,
-                       graphs=GRAPH_MODES[args.graphs])
-        ctxs.append(P)
-        vs.append(torch.zeros((3,) + tuple(w["n"]), dtype=torch.float32, device="cuda"))
-    torch.cuda.synchronize()
-
-    def solve_all():
-        for v in vs:
-            v.zero_()
-        torch.cuda.synchronize()
-        return ga.ga_solve_batch([P.ctx for P in ctxs], np.float32, vs)
-
-    for _ in range(args.warmup):
-        solve_all()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        stats, status = solve_all()
-    barrier()
-    dt, solved = aggregate_over_ranks(time.perf_counter() - t0, len(probs) * args.steps)
-    # the same problems solved one after another, for comparison
-    t1 = time.perf_counter()
-    for P, v in zip(ctxs, vs):
-        v.zero_()
-        torch.cuda.synchronize()
-        P.solve(v)
-    torch.cuda.synchronize()
-    seq = time.perf_counter() - t1
+    probs = batch_inputs(32, seed=rank)
+    res, dt = measure_batch(probs, args.graphs, args.steps, args.warmup, barrier)
+    dt, solved = aggregate_over_ranks(dt, len(probs) * args.steps)
     if ws > 1:
         torch.distributed.destroy_process_group()
     if rank != 0:
@@ -378,16 +486,21 @@ def run_batch(args):
             "value": solved / dt, "unit": "problems/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch: 32 problems, grids from {64,96,128,160}^3, nt=4, H1, alpha in {1e-2,1e-3}, "
-                                   "GA-NGMRES(5;4,2) to rel-grad 1e-2, " +
-                                   ("the whole batch one CUDA graph launch" if args.graphs == "device"
-                                    else "one stream per problem"),
-                       "graphs": args.graphs},
-            "sequential_s_per_batch": seq,
-            "per_problem": [{"n": int(w["n"][0]), "alpha": w["alpha"], "iters": st.iters,
-                             "grad_evals": st.grad_evals, "converged": bool(st.converged)}
-                            for w, st in zip(probs, stats)]}
+            "config": {"workload": BATCH_NAME + (", the whole batch one CUDA graph launch" if args.graphs == "device"
+                                                 else ", one stream per problem"), "graphs": args.graphs},
+            "gpu_launches": ga.ga_kernel_launches(), "per_problem": res["per_problem"]}
     print(json.dumps(line), flush=True)
+
+
+# Algorithmic HBM bytes per voxel of the 256^3 continuity workload (d = 3, FP32, n_t = 16, checkpoints
+# every 4 steps): a reduced gradient 4 [(22 + 1) n_t + 47] plus the checkpoint recompute
+# 3/4 (d + 2) 4 n_t (27.85 GB + 4.0 GB at 256^3), an objective-only evaluation (line-search trial)
+# 4 (5 n_t + 7) (5.84 GB), and per iteration the window's inner products and combination 2 (w + 2) d 4.
+def bytes_per_voxel(nt=NT, window=10, d=3, s=4):
+    grad = s * ((22 + 1) * nt + 47) + 0.75 * (d + 2) * s * nt
+    obj = s * (5 * nt + 7)
+    win = 2 * (window + 2) * d * s
+    return grad, obj, win
 
 
 def main():
@@ -417,8 +530,11 @@ def main():
                     help="also time the discretise-then-optimise gradient (advection transport, same data)")
     ap.add_argument("--compare-methods", action="store_true",
                     help="also time the same solve with GA-AA and RPGD (mixed precision, same settings)")
-    ap.add_argument("--fp64-tts", action="store_true",
-                    help="also time the same GA-NGMRES solve with the FP64 GPU path (slow: FP64 is ALU-bound on GB300)")
+    ap.add_argument("--no-fp64-tts", action="store_true",
+                    help="skip the same GA-NGMRES solve on the FP64 GPU path and the per-result error of the "
+                         "mixed path against it")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batch of 32 uneven advection problems (both batched forms)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -543,6 +659,15 @@ def main():
         tts = {"tts_s": time.perf_counter() - t0, "iters": stt.iters, "converged": bool(stt.converged),
                "rel_grad_inf": stt.rel_grad_inf, "grad_evals": stt.grad_evals, "obj_evals": stt.obj_evals,
                "pde_solves": stt.pde_solves, "mismatch": stt.mismatch, "obj": stt.obj, "error": err}
+        # roofline of the whole solve: algorithmic bytes of its evaluations and window operations
+        bg, bo, bw = bytes_per_voxel()
+        tb = (stt.grad_evals * bg + stt.obj_evals * bo + stt.iters * bw) * n ** 3
+        hbm_peak, kind = peaks()
+        tts["roofline"] = {"bound": "hbm", "algorithmic_bytes": tb, "achieved": round(tb / tts["tts_s"] / 1e9, 1),
+                           "peak": hbm_peak, "unit": "GB/s", "frac": round(tb / tts["tts_s"] / 1e9 / hbm_peak, 4),
+                           "model": "per voxel: gradient 4[23 nt + 47] + 3/4 (d+2) 4 nt (checkpoint recompute), "
+                                    "objective 4 (5 nt + 7), window 2 (w+2) d 4 per iteration",
+                           "peak_kind": kind}
 
     v_sol = v.clone()  # the GA-NGMRES solution (with --no-tts: the last timed iterate)
 
@@ -590,11 +715,9 @@ def main():
         del Pd, vd
         torch.cuda.empty_cache()
 
-    # ---- the same solve on the FP64 GPU path (optional) ----
+    # ---- the same solve on the FP64 GPU path, and the error of the mixed path against it ----
     fp64 = None
-    if args.fp64_tts:
-        P.close()
-        torch.cuda.empty_cache()
+    if not args.no_fp64_tts:
         d64 = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
         P64 = ga.Problem(d64(w["m0"]), d64(w["m1"]), prec="fp64", **SETTINGS)
         v64 = torch.zeros((3,) + shape, dtype=torch.float64, device="cuda")
@@ -605,17 +728,33 @@ def main():
             err = None
         except ga.GaError as e:
             err = str(e)
-            s64 = ga.Stats()
-            ga.lib().ga_get_stats(P64.ctx, s64)
+            s64 = P64.stats()
         torch.cuda.synchronize()
         fp64 = {"tts_s": time.perf_counter() - t0, "iters": s64.iters, "converged": bool(s64.converged),
                 "rel_grad_inf": s64.rel_grad_inf, "grad_evals": s64.grad_evals, "obj_evals": s64.obj_evals,
+                "mismatch": s64.mismatch, "obj": s64.obj,
                 "t_grad_ms_per_eval": s64.t_grad_ms / max(s64.grad_evals, 1), "error": err}
+        if tts is not None:
+            fp64["mixed_tts_speedup"] = fp64["tts_s"] / tts["tts_s"]
+            # error of the mixed path per result: objective and gradient at the mixed solution, against
+            # the FP64 GPU path at the same velocity (the FP64 path matches the oracle to 1e-10)
+            gm = torch.empty_like(v_sol)
+            g64 = torch.empty_like(v64)
+            vs64 = v_sol.double()
+            obj_m = P.gradient(v_sol, gm)
+            obj_64 = P64.gradient(vs64, g64)
+            ref_n = float(torch.linalg.vector_norm(g64))
+            fp64["mixed_vs_fp64_at_mixed_solution"] = {
+                "rel_l2_grad": float(torch.linalg.vector_norm(gm.double() - g64)) / ref_n,
+                "rel_err_obj": abs(obj_m - obj_64) / abs(obj_64),
+                "obj_mixed": obj_m, "obj_fp64": obj_64,
+                "rel_inf_grad": float((gm.double() - g64).abs().max() / g64.abs().max()),
+                "note": "g and obj of the mixed (FP32 fields, FP64 reductions) path and of the FP64 path, "
+                        "both on the GPU, at the mixed GA-NGMRES solution v (cast to FP64)"}
+            del gm, g64, vs64
         P64.close()
         del P64, v64
         torch.cuda.empty_cache()
-        P = ga.Problem(m0, m1, prec="mixed", **SETTINGS)
-        v.zero_()
 
     # ---- the same solve with the other methods of the paper's comparison (optional) ----
     methods = None
@@ -706,9 +845,27 @@ def main():
                "note": "timed: ga_setup from pinned host m0/m1 + K ga_step calls with a pinned host v "
                        "(v^(0) uploaded once, v^(k+1) read back every step) + ga_destroy; "
                        "h2d bytes are the job's uploads divided by K"}
+    # ---- the batched form (32 uneven advection problems): both forms, seeded per rank ----
+    batch = None
+    if not args.no_batch:
+        probs = batch_inputs(32, seed=rank)
+        batch = {"workload": BATCH_NAME}
+        for mode in ("off", "device"):
+            res, dt = measure_batch(probs, mode, 2, 1, barrier)
+            key = "host_workers" if mode == "off" else "one_graph_launch"
+            batch[key] = res
+        del probs
+        torch.cuda.empty_cache()
+
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
+        if tts is not None and cb.get("s_per_obj_1core_256"):
+            cb["tts_estimate_256_s"] = (tts["grad_evals"] * cb["s_per_grad_1core_256"] +
+                                        tts["obj_evals"] * cb["s_per_obj_1core_256"])
+            cb["tts_estimate_note"] = ("ESTIMATED oracle time to rel-grad 1e-2 at 256^3 on one core: seconds per "
+                                       "gradient and per objective (sample scaled by voxel count) x the GPU "
+                                       "solve's evaluation counts")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -721,7 +878,8 @@ def main():
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
                 "deriv_tiles_zyx": deriv_tiles,
-                "clocks": clocks, "tts": tts, "tts_device": tts_dev, "fp64_tts": fp64, "methods_tts": methods, "deformation": deformation, "dto": dto_res, "grad_only_evals_per_s": grad_only,
+                "clocks": clocks, "tts": tts, "tts_device": tts_dev, "fp64_tts": fp64, "batch": batch,
+                "methods_tts": methods, "deformation": deformation, "dto": dto_res, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in
                                                                        ("iters", "obj_evals", "rel_grad_inf", "obj",
                                                                         "rho_mem")}}

@@ -330,17 +330,29 @@ def workload(name, seed=0, n=None):
     raise ValueError(f"unknown workload {name!r}")
 
 
-def batch_workloads(count=32, seed=0, sizes=(64, 96, 128, 160)):
-    """Independent 3D advection problems of uneven size (nt=4, H1, alpha in {1e-2,1e-3})."""
+def batch_specs(count=32, seed=0, sizes=(64, 96, 128, 160)):
+    """(index, grid size, alpha, data seed) of each problem of a seeded batch: sizes drawn from
+    `sizes`, alpha from {1e-2, 1e-3}."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         ni = int(rng.choice(sizes))
         alpha = float(rng.choice([1e-2, 1e-3]))
-        w = workload("adv3d64", seed=seed * 1000 + i + 1, n=(ni, ni, ni))
-        w.update(name=f"batch{i}", reg_order=1, alpha=alpha, nt=4)
-        out.append(w)
+        out.append((i, ni, alpha, seed * 1000 + i + 1))
     return out
+
+
+def batch_problem(spec):
+    """One problem of a batch from its spec (batch_specs): the adv3d64 recipe at that size, nt=4, H1."""
+    i, ni, alpha, data_seed = spec
+    w = workload("adv3d64", seed=data_seed, n=(ni, ni, ni))
+    w.update(name=f"batch{i}", reg_order=1, alpha=alpha, nt=4)
+    return w
+
+
+def batch_workloads(count=32, seed=0, sizes=(64, 96, 128, 160)):
+    """Independent 3D advection problems of uneven size (nt=4, H1, alpha in {1e-2,1e-3})."""
+    return [batch_problem(sp) for sp in batch_specs(count, seed, sizes)]
 
 
 def random_problem_fields(n, seed, model="advection", vel_scale_vox=1.0, kmax_img=4, kmax_vel=3):

@@ -60,3 +60,16 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_cpu_baseline_runs_the_oracle_on_a_spawned_pool():
+    """The CPU baseline runs one unmodified oracle evaluation per core in spawned processes (safe after
+    a CUDA context exists) and scales the sample's rate to 256^3 by voxel count."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    cb = bench.cpu_baseline(n=16, cores=2)
+    assert cb["cores"] == 2 and cb["kind"] == "oracle"
+    assert cb["value"] > 0 and cb["s_per_grad_1core_256"] > 0 and cb["s_per_obj_1core_256"] > 0
+    # rate of 2 cores = 2 / (seconds per gradient at 256^3)
+    assert abs(cb["value"] * cb["s_per_grad_1core_256"] - 2.0) < 1e-9

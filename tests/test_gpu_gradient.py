@@ -54,6 +54,29 @@ def test_objective_and_gradient(shape, prec, model):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(32, 24), (16, 12, 20), (20, 24, 16)])
+def test_incompressible_h3_gradient_and_preconditioner(shape, prec):
+    """The incompressible runs of Sec. 3.6 use the H3 seminorm (L^ = |k|^6): gradient alpha L v + P b,
+    objective, and the projected preconditioner s = -(alpha L)^{-1} P g against the oracle."""
+    P, O, v = _setup(shape, prec, "incompressible", s=3, alpha=1e-4, nt=16 if len(shape) == 2 else 4, seed=3)
+    g = empty(v.shape, prec)
+    J = P.gradient(to_dev(v, prec), g)
+    gref, Jref = O.gradient(v)
+    tol = TOL[prec] if prec == "fp64" else TOL_GRAD_MIXED
+    if prec == "mixed":  # alpha L v from an FP32 transform of the caller's v (see the 512-axis test below)
+        L = osp.symbol_L(shape, 3)
+        amp = 1e-4 * np.sqrt(np.mean(L ** 2)) * np.linalg.norm(v.ravel())
+        tol += 6e-8 * np.log2(np.prod(shape)) * amp / np.linalg.norm(gref.ravel())
+    assert abs(J - Jref) <= max(tol, TOL_GRAD_MIXED) * abs(Jref)
+    assert rel_l2(host(g), gref) < tol, rel_l2(host(g), gref)
+    s_out = empty(v.shape, prec)
+    P.precond(g, s_out)
+    sref = O.precond(host(g))
+    assert rel_l2(host(s_out), sref) < TOL[prec] * 10
+    assert np.abs(osp.div(sref)).max() < 1e-10 * np.abs(sref).max()  # the direction stays divergence free
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("model", ["advection", "continuity"])
 def test_gradient_with_a_512_axis(prec, model):
     """A 512-point axis (the runtime-planned transform length of the 512^3 mesh study), H2. At a
