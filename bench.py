@@ -134,9 +134,10 @@ class ClockSampler:
 
 
 def make_inputs(n=N, seed=0):
+    """The benchmark recipe on an n^3 grid (n an int) or on a given (n0, n1, n2) grid."""
     from synth.inputs import workload
 
-    return workload("cont3d256", seed=seed, n=(n, n, n))
+    return workload("cont3d256", seed=seed, n=tuple(n) if isinstance(n, (tuple, list)) else (n, n, n))
 
 
 def _oracle_worker(job):
@@ -516,6 +517,8 @@ def main():
                     help="skip the device-driven (one graph launch) time-to-solution")
     ap.add_argument("--prof-class", type=int, default=PROF_SL_FWD)
     ap.add_argument("--grid", type=int, default=N, help="grid size (default 256; smaller only for smoke runs)")
+    ap.add_argument("--shape", default=None,
+                    help="n0,n1,n2 grid instead of --grid (small non-cubic cases for profiling captures)")
     ap.add_argument("--sweep-parts", default="hyper,alpha,mesh,inc",
                     help="--workload sweep: comma-separated subset of hyper, alpha, mesh, inc")
     ap.add_argument("--sweep-max-n", type=int, default=512, help="--workload sweep: largest mesh")
@@ -558,8 +561,8 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.grid
-    w = make_inputs(n)
-    shape = (n, n, n)
+    shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else (n, n, n)
+    w = make_inputs(shape)
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
     m0, m1 = dev(w["m0"]), dev(w["m1"])
     P = ga.Problem(m0, m1, prec="mixed", **SETTINGS)
@@ -606,7 +609,7 @@ def main():
     step_stats = st.as_dict()
 
     # ---- roofline of the dominant kernel: algorithmic bytes per launch / mean event duration ----
-    nv = n ** 3
+    nv = int(np.prod(shape))
     algo = {PROF_SL_FWD: ("sl_forward continuity step: read pi_j, mu, 3 displacement fields, write pi_{j+1}", 24),
             PROF_SL_ADJ: ("sl_adjoint continuity step: read lambda_{j+1}, 3 displacement fields, write lambda_j", 20),
             PROF_DERIV: ("fused FFT-derivative pass: read f, read multiplier, read+write accumulator", 16),
@@ -617,12 +620,14 @@ def main():
     per_launch_ms = prof_ms / max(prof_n, 1)
     bytes_per_launch = algo[1] * nv
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    sl_depth = ga.ga_op_get_sl_depth(P.ctx)  # brick depth of the transport steps chosen at setup
     traffic = None
-    if args.prof_class == PROF_SL_FWD and SL_FWD_TRAFFIC_192 is not None:
-        traffic = round(SL_FWD_TRAFFIC_192 * (n / 192.0) ** 3)
+    if args.prof_class == PROF_SL_FWD and SL_FWD_TRAFFIC_192 is not None and sl_depth == 8:
+        traffic = round(SL_FWD_TRAFFIC_192 * nv / 192.0 ** 3)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "traffic_note": "bytes per launch from an ncu capture at 192^3 scaled by voxel count",
+                "traffic_note": "bytes per launch from an ncu capture at 192^3 (brick depth 8) scaled by voxel "
+                                "count; null for another brick depth",
                 "kernel": algo[0],
                 "bytes_per_launch": bytes_per_launch, "launches": prof_n, "mean_launch_ms": per_launch_ms,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"}
@@ -661,7 +666,7 @@ def main():
                "pde_solves": stt.pde_solves, "mismatch": stt.mismatch, "obj": stt.obj, "error": err}
         # roofline of the whole solve: algorithmic bytes of its evaluations and window operations
         bg, bo, bw = bytes_per_voxel()
-        tb = (stt.grad_evals * bg + stt.obj_evals * bo + stt.iters * bw) * n ** 3
+        tb = (stt.grad_evals * bg + stt.obj_evals * bo + stt.iters * bw) * nv
         hbm_peak, kind = peaks()
         tts["roofline"] = {"bound": "hbm", "algorithmic_bytes": tb, "achieved": round(tb / tts["tts_s"] / 1e9, 1),
                            "peak": hbm_peak, "unit": "GB/s", "frac": round(tb / tts["tts_s"] / 1e9 / hbm_peak, 4),
@@ -871,13 +876,13 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD_NAME, "grid": [n, n, n], "nt": NT, "precision":
+                "config": {"workload": WORKLOAD_NAME, "grid": list(shape), "nt": NT, "precision":
                            "FP32 fields/transport/FFT, FP64 compensated reductions, Gram and least squares",
                            "step": "one GA-NGMRES iteration (ga_step) of a solve from v=0",
                            "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-                "deriv_tiles_zyx": deriv_tiles,
+                "deriv_tiles_zyx": deriv_tiles, "sl_brick_depth": sl_depth,
                 "clocks": clocks, "tts": tts, "tts_device": tts_dev, "fp64_tts": fp64, "batch": batch,
                 "methods_tts": methods, "deformation": deformation, "dto": dto_res, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in

@@ -84,6 +84,8 @@ _SIGS = {
     "ga_op_div": ([_vp, _vp, _vp], _c_int),
     "ga_op_get_tiles": ([_vp, ctypes.POINTER(_c_int)], _c_int),
     "ga_op_set_tiles": ([_vp, ctypes.POINTER(_c_int)], _c_int),
+    "ga_op_get_sl_depth": ([_vp, ctypes.POINTER(_c_int)], _c_int),
+    "ga_op_set_sl_depth": ([_vp, _c_int], _c_int),
     "ga_op_fft_r2c": ([_vp, _vp, _vp], _c_int),
     "ga_op_fft_c2r": ([_vp, _vp, _vp], _c_int),
     "ga_op_apply_L": ([_vp, _vp, _vp], _c_int),
@@ -397,6 +399,17 @@ def ga_op_get_tiles(ctx, dim):
     arr = (_c_int * (2 * dim))()
     _check(lib().ga_op_get_tiles(ctx, arr), ctx)
     return list(arr)
+
+
+def ga_op_get_sl_depth(ctx):
+    """Brick depth (z voxels per thread) of the FP32 3D transport steps chosen by the autotuner."""
+    d = _c_int()
+    _check(lib().ga_op_get_sl_depth(ctx, ctypes.byref(d)), ctx)
+    return d.value
+
+
+def ga_op_set_sl_depth(ctx, depth):
+    _check(lib().ga_op_set_sl_depth(ctx, int(depth)), ctx)
 
 
 def ga_op_set_tiles(ctx, pencils):

@@ -39,6 +39,7 @@ struct Grid {
   int n2h;                // n[2] / 2 + 1 (half spectrum along the contiguous axis)
   long long nvox;         // n0 * n1 * n2
   long long nhalf;        // n0 * n1 * n2h
+  int sl_bz = 8;          // brick depth (z voxels per thread) of the FP32 3D transport steps
   GA_HD int axis_of(int c) const { return 3 - dim + c; }
 };
 

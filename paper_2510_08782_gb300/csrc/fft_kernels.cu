@@ -399,6 +399,145 @@ k_deriv_cols(DerivIO<T> io, int Lr, long long S, long long outer_stride, int nx,
   }
 }
 
+// ---- register-resident derivative passes for 256-point axes -----------------------------------
+// A 256-point transform as 16 x 16 (the four-step form): with n = q + 16 m and k = k2 + 16 k1,
+//   X[k2 + 16 k1] = sum_q W16^(q k1) W256^(q k2) sum_m x[q + 16 m] W16^(m k2).
+// 256 threads transform 16 complex pencils. In the load phase thread (p, q) holds x[q + 16 m] of
+// pencil p (m = 0..15) in registers and applies the inner DFT16 over m and the twiddles W256^(q k2);
+// one exchange through shared memory gives thread (p, k2) the values over q, whose DFT16 yields
+// X[k2 + 16 k1] in registers. There the derivative symbol i k~ is applied, and the inverse runs the
+// same steps backwards (DFT16 over k1 with conjugate weights, twiddles W256^(-n1 k2), one exchange,
+// DFT16 over k2), leaving thread (p, n1) with the derivative at n1 + 16 n2, n2 = 0..15: the positions
+// it loaded. Every index is a compile-time constant or a per-thread constant, and each element
+// passes through shared memory twice. The exchange buffer holds entry (p, i, j) at p*273 + i*17 + j
+// (complex units); the lanes of a warp differ either in p or in the fastest index of the global
+// layout, and both strides are odd, so the exchanges are free of bank conflicts.
+// ROWS: pencils along the contiguous axis (row p of the tile; the lanes of a half-warp cover
+// consecutive elements); otherwise pencils along a strided axis (columns; the lanes of a half-warp
+// cover consecutive columns). PAIR: pencil p is f + i f2 of one row/column (two time steps of the body
+// force); otherwise pencil p packs rows/columns 2p and 2p + 1 of f.
+constexpr int kX16P = 16 * 17 + 1;  // pencil stride of the exchange buffer
+
+template <typename T> __device__ __forceinline__ void idft16(cx<T>* a) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i].y = -a[i].y;
+  dft16<T>(a);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i].y = -a[i].y;
+}
+
+// The derivative of 16 complex pencils held in registers (see above): on entry thread (p, x) holds
+// x[x + 16 m] of its pencil in a[m]; on return a[n2] holds 256 times the derivative at x + 16 n2.
+// tw: W256^j in shared memory; xp: this pencil's exchange area. Contains the CTA barriers of the two
+// exchanges, so every thread of the CTA calls it.
+template <typename T>
+__device__ __forceinline__ void reg256_deriv(cx<T>* a, const cx<T>* tw, cx<T>* xp, int x) {
+  // load phase: DFT16 over m, twiddles W256^(q k2), exchange
+  dft16<T>(a);
+#pragma unroll
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) xp[k2 * 17 + x] = a[k2];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = xp[x * 17 + q];  // thread now holds k2 = x over q
+  dft16<T>(a);                                          // a[k1] = X[x + 16 k1]
+  // derivative symbol i k~ (zero at the Nyquist index 128)
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    const int k = x + 16 * k1;
+    const T kt = (k == 128) ? T(0) : (k < 128 ? T(k) : T(k - 256));
+    a[k1] = mk<T>(-kt * a[k1].y, kt * a[k1].x);
+  }
+  // inverse: DFT16 over k1 with conjugate weights, twiddles W256^(-n1 k2), exchange, DFT16 over k2
+  idft16<T>(a);  // a[n1]
+#pragma unroll
+  for (int n1 = 1; n1 < 16; ++n1) a[n1] = cmul(a[n1], cconj(tw[n1 * x]));
+  __syncthreads();  // every thread has read its exchange entries
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) xp[n1 * 17 + x] = a[n1];
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) a[k2] = xp[x * 17 + k2];  // thread holds n1 = x over k2
+  idft16<T>(a);                                              // a[n2]: derivative at x + 16 n2
+}
+
+template <typename T, bool PAIR, bool ROWS>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_deriv_reg256(DerivIO<T> io, long long npen, long long S, long long outer_stride, const cx<T>* __restrict__ twg) {
+  constexpr int L = 256;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);  // W256^j, j < 256
+  cx<T>* xb = tw + L;                               // exchange buffer
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x;
+  const int p = ROWS ? (t >> 4) : (t & 15);  // complex pencil of the tile
+  const int x = ROWS ? (t & 15) : (t >> 4);  // q, then k2, then n1
+  constexpr int RP = PAIR ? 1 : 2;           // real rows/columns of f per complex pencil
+  // global offset of element x of this thread's (first) real pencil; element x + 16 m is at
+  // off + m * st16, the partner pencil (non-PAIR) pstride further
+  const long long r0 = (long long)blockIdx.x * 16 * RP + RP * p;
+  const bool v0 = r0 < npen, v1 = !PAIR && r0 + 1 < npen;
+  const long long off = ROWS ? r0 * L + x : (long long)blockIdx.y * outer_stride + r0 + (long long)x * S;
+  const long long st16 = ROWS ? 16 : 16 * S;
+  const long long pstride = ROWS ? L : 1;
+  // the operands of the output phase are read after the transforms: request their lines into L2 now
+  if (v0) {
+#pragma unroll 4
+    for (int m = 0; m < 16; ++m) {
+      const long long e = off + m * st16;
+      if (io.mult) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(io.mult + e));
+      if (PAIR && io.mult2) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(io.mult2 + e));
+      if (io.accumulate) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(io.out + e));
+    }
+  }
+  cx<T> a[16];
+  {
+    const T* fp = io.f + off;
+    const T* f2p = PAIR ? io.f2 + off : io.f + off + pstride;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      if (PAIR) {
+        a[m] = v0 ? mk<T>(fp[0], f2p[0]) : mk<T>(T(0), T(0));
+      } else {
+        a[m] = mk<T>(v0 ? fp[0] : T(0), v1 ? f2p[0] : T(0));
+      }
+      fp += st16;
+      f2p += st16;
+    }
+  }
+  __syncthreads();  // twiddle table
+  reg256_deriv<T>(a, tw, xb + p * kX16P, x);
+  const T inv = T(1) / T(L);
+  long long e = off;
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2, e += st16) {
+    const T re = a[n2].x * inv, im = a[n2].y * inv;
+    if (PAIR) {
+      if (!v0) continue;
+      T w1 = io.coef * re;
+      if (io.mult) w1 *= io.mult[e];
+      if (io.accumulate) w1 += io.out[e];
+      T w2 = io.coef2 * im;
+      if (io.mult2) w2 *= io.mult2[e];
+      io.out[e] = w2 + w1;
+    } else {
+      if (v0) {
+        T w = io.coef * re;
+        if (io.mult) w *= io.mult[e];
+        if (io.accumulate) w += io.out[e];
+        io.out[e] = w;
+      }
+      if (v1) {
+        T w = io.coef * im;
+        if (io.mult) w *= io.mult[e + pstride];
+        if (io.accumulate) w += io.out[e + pstride];
+        io.out[e + pstride] = w;
+      }
+    }
+  }
+}
+
 // ---- real-to-complex FFT of row pairs ---------------------------------------------------------
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
@@ -604,6 +743,38 @@ static cudaError_t deriv_pass(const Grid& g, const FftTables<T>& ft, int axis, c
   if (L == 1) {  // a singleton axis carries only k = 0: the derivative is zero
     if (io.accumulate) return cudaSuccess;
     return cudaMemsetAsync(io.out, 0, sizeof(T) * g.nvox, st);
+  }
+  if (L == kRegFftLen) {  // register-resident transform (k_deriv_reg256)
+    const size_t sm = sizeof(cx<T>) * (256 + 16 * kX16P);
+    constexpr int rp = PAIR ? 1 : 2;
+    if (axis == 2) {
+      const long long rows = (long long)g.n[0] * g.n[1];
+      auto kern = k_deriv_reg256<T, PAIR, true>;
+      cudaError_t e = allow_smem(kern, sm);
+      if (e != cudaSuccess) return e;
+      note_launches(1);
+      kern<<<(unsigned)((rows + 16 * rp - 1) / (16 * rp)), 256, sm, st>>>(io, rows, 1, 0, ft.tw[2]);
+      return cudaGetLastError();
+    }
+    const int nx = g.n[2];
+    long long S, outer_stride;
+    int outer;
+    if (axis == 1) {
+      S = nx;
+      outer = g.n[0];
+      outer_stride = (long long)g.n[1] * nx;
+    } else {
+      S = (long long)g.n[1] * nx;
+      outer = g.n[1];
+      outer_stride = nx;
+    }
+    auto kern = k_deriv_reg256<T, PAIR, false>;
+    cudaError_t e = allow_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    kern<<<dim3((unsigned)((nx + 16 * rp - 1) / (16 * rp)), (unsigned)outer), 256, sm, st>>>(io, nx, S, outer_stride,
+                                                                                            ft.tw[axis]);
+    return cudaGetLastError();
   }
   const int tuned = PAIR ? ft.pair_pencils[axis] : ft.deriv_pencils[axis];
   int B = tuned > 0 ? tuned : deriv_batch<T>(L);

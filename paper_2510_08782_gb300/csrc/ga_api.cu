@@ -300,8 +300,8 @@ template <typename T> struct Engine : EngineBase {
   // result depends on the choice.
   void autotune_tiles() {
     static std::mutex mu;
-    static std::map<std::vector<int>, std::array<int, 6>> cache;
-    const std::vector<int> key = {(int)sizeof(T), g.n[0], g.n[1], g.n[2]};
+    static std::map<std::vector<int>, std::array<int, 7>> cache;
+    const std::vector<int> key = {(int)sizeof(T), g.n[0], g.n[1], g.n[2], model};
     {
       std::lock_guard<std::mutex> lk(mu);
       auto it = cache.find(key);
@@ -310,15 +310,21 @@ template <typename T> struct Engine : EngineBase {
           ft.deriv_pencils[a] = it->second[a];
           ft.pair_pencils[a] = it->second[3 + a];
         }
+        g.sl_bz = it->second[6];
         return;
       }
     }
-    std::array<int, 6> best = {0, 0, 0, 0, 0, 0};
+    std::array<int, 7> best = {0, 0, 0, 0, 0, 0, 8};
     for (int pair = 0; pair < 2; ++pair) {
       for (int a = 3 - dim; a < 3; ++a) {
         const int L = g.n[a];
         if (L == 1) continue;
         int* slot = pair ? &ft.pair_pencils[a] : &ft.deriv_pencils[a];
+        if (L == kRegFftLen) {  // the register-resident transform: a fixed tile, nothing to tune
+          *slot = kRegFftPencils;
+          best[3 * pair + a] = kRegFftPencils;
+          continue;
+        }
         const int b0 = deriv_default_pencils<T>(L);
         float best_ms = 0.f;
         int choice = 0;
@@ -344,6 +350,35 @@ template <typename T> struct Engine : EngineBase {
         *slot = choice;
         best[3 * pair + a] = choice;
       }
+    }
+    // Brick depth of the FP32 3D transport steps: one state and one adjoint step of this model per
+    // candidate, at zero displacement (the shared-memory gather every in-halo voxel takes).
+    if (std::is_same<T, float>::value && dim == 3) {
+      ck(cudaMemsetAsync(xm, 0, sizeof(T) * vl, st), "memset");
+      ck(cudaMemsetAsync(xp, 0, sizeof(T) * vl, st), "memset");
+      ck(cudaMemsetAsync(this->mu, 0, sizeof(T) * nv, st), "memset");
+      float best_ms = 0.f;
+      int choice = 0;
+      for (int zb : kSlDepths) {
+        g.sl_bz = zb;
+        sl_forward(m0, tmp[0]);  // loads the kernels
+        sl_adjoint(m1, tmp[1]);
+        ck(cudaEventRecord(ev[0], st), "event");
+        for (int r = 0; r < 2; ++r) {
+          sl_forward(m0, tmp[0]);
+          sl_adjoint(m1, tmp[1]);
+        }
+        ck(cudaEventRecord(ev[1], st), "event");
+        ck(cudaEventSynchronize(ev[1]), "event sync");
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
+        if (choice == 0 || ms < best_ms) {
+          choice = zb;
+          best_ms = ms;
+        }
+      }
+      g.sl_bz = choice;
+      best[6] = choice;
     }
     std::lock_guard<std::mutex> lk(mu);
     cache.emplace(key, best);
@@ -1847,8 +1882,30 @@ ga_status ga_op_get_tiles(const ga_ctx* ctx, int* pencils) {
       const int p = ctx->ef ? (pair ? ctx->ef->ft.pair_pencils[a] : ctx->ef->ft.deriv_pencils[a])
                             : (pair ? ctx->ed->ft.pair_pencils[a] : ctx->ed->ft.deriv_pencils[a]);
       pencils[pair * dim + c] =
-          p > 0 ? p : (ctx->ef ? ga::deriv_default_pencils<float>(L) : ga::deriv_default_pencils<double>(L));
+          L == ga::kRegFftLen
+              ? ga::kRegFftPencils
+              : (p > 0 ? p : (ctx->ef ? ga::deriv_default_pencils<float>(L) : ga::deriv_default_pencils<double>(L)));
     }
+  return GA_OK;
+}
+
+ga_status ga_op_get_sl_depth(const ga_ctx* ctx, int* depth) {
+  if (!ctx || !depth) return GA_ERR_ARG;
+  *depth = ctx->ef ? ctx->ef->g.sl_bz : ctx->ed->g.sl_bz;
+  return GA_OK;
+}
+
+ga_status ga_op_set_sl_depth(ga_ctx* ctx, int depth) {
+  if (!ctx) return GA_ERR_ARG;
+  if (depth == 0) depth = 8;
+  bool known = false;
+  for (int d : ga::kSlDepths) known = known || d == depth;
+  if (!known) {
+    set_err(ctx, "ga_op_set_sl_depth: brick depth %d is not one of 4, 8, 12", depth);
+    return GA_ERR_ARG;
+  }
+  if (ctx->ef) ctx->ef->g.sl_bz = depth;
+  else ctx->ed->g.sl_bz = depth;
   return GA_OK;
 }
 

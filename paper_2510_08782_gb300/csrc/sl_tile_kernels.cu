@@ -106,7 +106,6 @@ constexpr int TILEA = TXA * TY * TZ;
 // Measured at 256^3: 48 -> 0.334 ms, 40 -> 0.345 ms, 41 -> 0.361 ms, 44 -> 0.364 ms. 3 CTAs of
 // 75 KB still fit on an SM.
 constexpr int TXP = 48;
-constexpr int TILEP = TXP * TY * TZ;
 
 struct BrickIdx {
   int bx, by, bz;
@@ -119,10 +118,19 @@ __device__ __forceinline__ BrickIdx brick_of(int b, int nbx, int nby) {
   return r;
 }
 
+// Tile planes and elements of a brick of depth ZB (z voxels per thread).
+template <int ZB> struct Tile {
+  static constexpr int TZ = ZB + 2 * H + 2;
+  static constexpr int A = TXA * TY * TZ;  // floats of one staged field
+  static constexpr int P = TXP * TY * TZ;  // (f, f mu) pairs of the two-field steps
+};
+
 // Issue the copies of one brick's tile of `src` into `dst` (all threads of the CTA).
+template <int ZB = BZ>
 __device__ __forceinline__ void stage_async(float* dst, const float* __restrict__ src, const BrickIdx& bi, int n0,
                                             int n1, int n2, bool vec) {
-  const int gx0 = bi.bx * BX - XOFF, gy0 = bi.by * BY - H - 1, gz0 = bi.bz * BZ - H - 1;
+  constexpr int TZ = Tile<ZB>::TZ, TILEA = Tile<ZB>::A;
+  const int gx0 = bi.bx * BX - XOFF, gy0 = bi.by * BY - H - 1, gz0 = bi.bz * ZB - H - 1;
   if (vec) {  // 16-byte chunks: n2 % 4 == 0 and n2 >= TXA, so a chunk never straddles the wrap;
               // the launcher also requires n1 >= TY and n0 >= TZ so one conditional shift wraps y, z
     for (int c = threadIdx.x; c < TY * TZ * (TXA / 4); c += blockDim.x) {
@@ -237,11 +245,12 @@ __device__ __forceinline__ void sl_single(const float* __restrict__ f, const flo
 // once per tile element. Each thread walks its column of 8 voxels two at a time: the pair's weights
 // and its 64-tap sums (per field) run as packed FP32x2 operations, with the taps read from shared
 // memory at compile-time offsets from one base index per voxel.
-template <int MODE>
+template <int MODE, int ZB>
 __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const float* __restrict__ mu,
                                              const float* __restrict__ disp, float* __restrict__ out, int n0, int n1,
                                              int n2, float ht, int vec) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;  // staged fields: f (and f * mu)
+  constexpr int TILEA = Tile<ZB>::A;
   extern __shared__ __align__(16) float smem[];
   const float* sf = smem;
   const float2* sp = reinterpret_cast<const float2*>(smem);  // two-field steps: (f, f mu) per element
@@ -249,14 +258,14 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
   const long long plane = (long long)n1 * n2;
   const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
   const BrickIdx bi = brick_of(blockIdx.x, nbx, nby);
-  stage_async(smem, f, bi, n0, n1, n2, vec != 0);
-  if (NF == 2) stage_async(smem + TILEA, mu, bi, n0, n1, n2, vec != 0);
+  stage_async<ZB>(smem, f, bi, n0, n1, n2, vec != 0);
+  if (NF == 2) stage_async<ZB>(smem + TILEA, mu, bi, n0, n1, n2, vec != 0);
   cp_async_commit();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gx = bi.bx * BX + lane, gy = bi.by * BY + warp;
   const bool active = gx < n2 && gy < n1;
-  const int nz = min(BZ, n0 - bi.bz * BZ);
-  const long long idx0 = ((long long)(bi.bz * BZ) * n1 + gy) * n2 + gx;
+  const int nz = min(ZB, n0 - bi.bz * ZB);
+  const long long idx0 = ((long long)(bi.bz * ZB) * n1 + gy) * n2 + gx;
   // Displacements (and mu at the voxel) of one pair ahead are kept in registers: the first pair's are
   // requested while the tile is still being copied, each later pair's while the previous one is
   // interpolated.
@@ -344,35 +353,141 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
         out[ib] = step_value<MODE>(P.y, 0.f, cmb, ht);
       }
     } else {
-      sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * BZ + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
-      sl_single<MODE>(f, mu, out, sf, col, ib, bi.bz * BZ + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
+      sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * ZB + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
+      sl_single<MODE>(f, mu, out, sf, col, ib, bi.bz * ZB + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
     }
   }
   if (v < nz) {
     const long long ia = idx0 + v * plane;
-    sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * BZ + v, v, gy, gx, disp[ia], disp[nv + ia], disp[2 * nv + ia],
+    sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * ZB + v, v, gy, gx, disp[ia], disp[nv + ia], disp[2 * nv + ia],
                     n0, n1, n2, ht);
   }
 }
 
+// ---- column-reuse gather ------------------------------------------------------------------------
+// With departure points less than a cell or so from the arrival points, the stencil base offsets
+// (floors) of a thread's column of BZ voxels take at most two neighbouring values per axis. Each
+// voxel's 4 x 4 x 4 stencil then lies in the column's padded 5 x 5 x 5 window: the base B is the
+// smaller floor and a voxel whose floor is B + 1 takes its cubic weights shifted by one, with a zero
+// in front (others end in a zero). The thread walks the BZ + 4 planes of the column once, reads each
+// plane's 5 x 5 patch of (y, x) taps from shared memory once, and accumulates it into every voxel
+// whose padded z-window holds that plane: 25 x (BZ + 4) / BZ = 37.5 taps per voxel instead of 64.
+// The extra terms are exact zeros (w * t with w = 0 adds nothing), and the remaining products and
+// sums run in the order of the per-voxel gather (x, then y, then z, first term a product), so every
+// value equals the per-voxel gather's bit for bit. The walk trades shared-memory reads for FMAs
+// (125 instead of 64 per field and voxel): it pays in the departure-point kernel, whose three velocity
+// interpolants per sign share one stencil, and not in the one- and two-field transport steps, which
+// keep the per-voxel gather.
+
+// Column bases of one axis: B = min(floor) (or 0 when every floor is 1), valid when every floor is
+// B or B + 1 and the padded window [B - 1, B + 3] stays inside the staged halo.
+__device__ __forceinline__ bool column_base(float lo, float hi, int& B) {
+  B = (int)fminf(lo, 0.f);
+  return lo >= -(float)H && hi <= (float)(H - 1) && hi - lo <= 1.f;
+}
+
+// Padded weights of one axis: the cubic weights at t, placed at [sel, sel + 4) of five.
+__device__ __forceinline__ void padded5(float t, bool sel, float* w5) {
+  float w[4];
+  lagrange4v(t, w);
+  w5[0] = sel ? 0.f : w[0];
+  w5[1] = sel ? w[0] : w[1];
+  w5[2] = sel ? w[1] : w[2];
+  w5[3] = sel ? w[2] : w[3];
+  w5[4] = sel ? w[3] : 0.f;
+}
+
+// The whole column of BZ voxels of one thread by the padded-window walk, for NF fields that share the
+// interpolation weights: disp(v, d) gives voxel v's displacement (z, y, x; cells), tap(i, t) reads the
+// NF fields' values at tile index i (tile pitch PT) into t[0..NF), and emit(v, acc) receives voxel v's
+// NF interpolants once its five planes are summed. Returns false, having done nothing, unless every
+// active lane of the warp qualifies (the caller then gathers voxel by voxel).
+template <int NF, int PT, typename Disp, typename Tap, typename Emit>
+__device__ __forceinline__ bool column_walk(int col, Disp&& disp, Tap&& tap, Emit&& emit) {
+  float lz = 1e30f, hz = -1e30f, ly = 1e30f, hy = -1e30f, lx = 1e30f, hx = -1e30f;
+#pragma unroll
+  for (int v = 0; v < BZ; ++v) {
+    float d[3];
+    disp(v, d);
+    const float a = floorf(d[0]), b = floorf(d[1]), c = floorf(d[2]);
+    lz = fminf(lz, a), hz = fmaxf(hz, a);
+    ly = fminf(ly, b), hy = fmaxf(hy, b);
+    lx = fminf(lx, c), hx = fmaxf(hx, c);
+  }
+  int Bz, By, Bx;
+  bool ok = column_base(lz, hz, Bz);
+  ok = column_base(ly, hy, By) && ok;
+  ok = column_base(lx, hx, Bx) && ok;
+  // NaN displacements fail every comparison above, so such a column takes the per-voxel path
+  if (!__all_sync(__activemask(), ok)) return false;
+  // tile index of the first padded tap of voxel 0
+  const int base = col + ((H + Bz) * TY + By) * PT + Bx;
+  float wx[BZ][5], wy[BZ][5], wz[BZ][5];
+  float acc[BZ][NF];
+#pragma unroll
+  for (int P = 0; P < BZ + 4; ++P) {
+    if (P < BZ) {  // voxel P enters: its padded weights
+      float d[3];
+      disp(P, d);
+      const float fz = floorf(d[0]), fy = floorf(d[1]), fx = floorf(d[2]);
+      padded5(d[0] - fz, fz > (float)Bz, wz[P]);
+      padded5(d[1] - fy, fy > (float)By, wy[P]);
+      padded5(d[2] - fx, fx > (float)Bx, wx[P]);
+    }
+    float ys[BZ][NF];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      float t[5][NF];
+      const int o = base + (P * TY + b) * PT;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) tap(o + a, t[a]);
+#pragma unroll
+      for (int v = 0; v < BZ; ++v) {
+        if (v > P || v < P - 4) continue;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          float r = __fmul_rn(t[0][f], wx[v][0]);
+          r = __fmaf_rn(t[1][f], wx[v][1], r);
+          r = __fmaf_rn(t[2][f], wx[v][2], r);
+          r = __fmaf_rn(t[3][f], wx[v][3], r);
+          r = __fmaf_rn(t[4][f], wx[v][4], r);
+          ys[v][f] = b == 0 ? __fmul_rn(r, wy[v][0]) : __fmaf_rn(r, wy[v][b], ys[v][f]);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < BZ; ++v) {
+      if (v > P || v < P - 4) continue;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        acc[v][f] = P == v ? __fmul_rn(ys[v][f], wz[v][0]) : __fmaf_rn(ys[v][f], wz[v][P - v], acc[v][f]);
+    }
+    if (P >= 4) emit(P - 4, acc[P - 4]);  // voxel P - 4 has seen its five planes
+  }
+  return true;
+}
+
 // Two-field steps (MODE 1, 2) fit 3 CTAs per SM by shared memory; one-field steps (MODE 0, 3) fit 4
 // when held to 64 registers.
-template <int MODE>
-__global__ void __launch_bounds__(256, 3) k_sl_tile2(const float* __restrict__ f, const float* __restrict__ mu,
-                                                  const float* __restrict__ disp, float* __restrict__ out, int n0,
-                                                  int n1, int n2, float ht, int vec) {
-  sl_tile_body<MODE>(f, mu, disp, out, n0, n1, n2, ht, vec);
+template <int MODE, int ZB>
+__global__ void __launch_bounds__(256, ZB <= 8 ? 3 : 2) k_sl_tile2(const float* __restrict__ f,
+                                                                  const float* __restrict__ mu,
+                                                                  const float* __restrict__ disp,
+                                                                  float* __restrict__ out, int n0, int n1, int n2,
+                                                                  float ht, int vec) {
+  sl_tile_body<MODE, ZB>(f, mu, disp, out, n0, n1, n2, ht, vec);
 }
-template <int MODE>
+template <int MODE, int ZB>
 __global__ void __launch_bounds__(256, 4) k_sl_tile1(const float* __restrict__ f, const float* __restrict__ mu,
                                                      const float* __restrict__ disp, float* __restrict__ out, int n0,
                                                      int n1, int n2, float ht, int vec) {
-  sl_tile_body<MODE>(f, mu, disp, out, n0, n1, n2, ht, vec);
+  sl_tile_body<MODE, ZB>(f, mu, disp, out, n0, n1, n2, ht, vec);
 }
 
 // RK2 departure points (displacements in cells) for 3D FP32 grids: X* = x -/+ h_t v(x), then
 // X-/+ = x -/+ (h_t / 2)(v(x) + I[v](X*)). The three velocity components of the brick + halo are
-// staged in shared memory; the three interpolants at X* share one stencil. Each thread walks its
+// staged in shared memory; the three interpolants at X* share one stencil. A full column whose warp
+// qualifies takes the padded-window walk (column_walk) for each sign; otherwise each thread walks its
 // column two voxels at a time: a pair's weights and its 64-tap sums run as packed FP32x2 operations
 // (interp64, as in the state steps). A voxel done alone (odd column length, or a stencil beyond the
 // halo in the pair) repeats the same operations in scalar form, so its value does not depend on the
@@ -385,7 +500,7 @@ k_departure_tile(const float* __restrict__ v, float* __restrict__ xm, float* __r
   const long long plane = (long long)n1 * n2;
   const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
   const BrickIdx bi = brick_of(blockIdx.x, nbx, nby);
-  for (int c = 0; c < 3; ++c) stage_async(smem + c * TILEA, v + c * nv, bi, n0, n1, n2, vec != 0);
+  for (int c = 0; c < 3; ++c) stage_async<BZ>(smem + c * TILEA, v + c * nv, bi, n0, n1, n2, vec != 0);
   cp_async_commit();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gx = bi.bx * BX + lane, gy = bi.by * BY + warp;
@@ -434,6 +549,22 @@ k_departure_tile(const float* __restrict__ v, float* __restrict__ xm, float* __r
   for (int sg = 0; sg < (both ? 2 : 1); ++sg) {
     const float sign = sg == 0 ? 1.f : -1.f;
     float* o = sg == 0 ? xm : xp;
+    if (nz == BZ) {  // the column walk over the three velocity tiles (X* within a cell or so)
+      auto disp = [&](int vz, float* d) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = -sign * ht * center(vz, k) * ih[k];
+      };
+      auto tap = [&](int i, float* t) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) t[k] = smem[k * TILEA + i];
+      };
+      auto emit = [&](int vz, const float* acc) {
+        const long long idx = idx0 + vz * plane;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o[k * nv + idx] = -sign * 0.5f * ht * (center(vz, k) + acc[k]) * ih[k];
+      };
+      if (column_walk<3, TXA>(col, disp, tap, emit)) continue;
+    }
     int vz = 0;
 #pragma unroll 1
     for (; vz + 1 < nz; vz += 2) {
@@ -472,29 +603,41 @@ k_departure_tile(const float* __restrict__ v, float* __restrict__ xm, float* __r
   }
 }
 
-template <int MODE>
-cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
-                        cudaStream_t st) {
+template <int MODE, int ZB>
+cudaError_t launch_mode_zb(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
+                           cudaStream_t st) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
+  constexpr int TILEA = Tile<ZB>::A, TILEP = Tile<ZB>::P;
   // two-field steps: the f and mu tiles, then the same bytes (plus row padding) as (f, f mu) pairs
   const size_t sm = NF == 2 ? sizeof(float) * (2 * TILEP > 2 * TILEA ? 2 * TILEP : 2 * TILEA) : sizeof(float) * TILEA;
   void (*kern)(const float*, const float*, const float*, float*, int, int, int, float, int);
-  if constexpr (NF == 2) kern = k_sl_tile2<MODE>;
-  else kern = k_sl_tile1<MODE>;
+  if constexpr (NF == 2) kern = k_sl_tile2<MODE, ZB>;
+  else kern = k_sl_tile1<MODE, ZB>;
   static std::atomic<bool> attr{false};
   if (!attr.load()) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr.store(true);
   }
-  const int nb = ((g.n[2] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[0] + BZ - 1) / BZ);
+  const int nb = ((g.n[2] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[0] + ZB - 1) / ZB);
   // 16-byte copies need n2 % 4 == 0 (rows of whole chunks), no chunk across the periodic seam
   // (n2 >= TXA) and 16-byte aligned field pointers
   const bool aligned = ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(mu ? mu : f)) & 15u) == 0;
-  const int vec = (g.n[2] % 4 == 0 && g.n[2] >= TXA && g.n[1] >= TY && g.n[0] >= TZ && aligned) ? 1 : 0;
+  const int vec = (g.n[2] % 4 == 0 && g.n[2] >= TXA && g.n[1] >= TY && g.n[0] >= Tile<ZB>::TZ && aligned) ? 1 : 0;
   note_launches(1);
   kern<<<nb, kTileThreads, sm, st>>>(f, mu, disp, out, g.n[0], g.n[1], g.n[2], ht, vec);
   return cudaGetLastError();
+}
+
+// Brick depths the setup autotuner chooses from (Grid::sl_bz); every depth gives the same values.
+template <int MODE>
+cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
+                        cudaStream_t st) {
+  switch (g.sl_bz) {
+    case 4: return launch_mode_zb<MODE, 4>(g, f, mu, disp, out, ht, st);
+    case 12: return launch_mode_zb<MODE, 12>(g, f, mu, disp, out, ht, st);
+    default: return launch_mode_zb<MODE, 8>(g, f, mu, disp, out, ht, st);
+  }
 }
 
 }  // namespace

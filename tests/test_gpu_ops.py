@@ -117,6 +117,35 @@ def test_fft_and_derivatives_on_long_axes(shape, prec):
         assert rel_l2(host(out), gref[a]) < TOL[prec] * 4, (a, rel_l2(host(out), gref[a]))
 
 
+AXES_256 = [(256, 6, 10), (4, 256, 18), (6, 10, 256), (5, 9, 256)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", AXES_256)
+def test_register_transform_on_256_axes(shape, prec):
+    """The register-resident derivative passes of 256-point axes: along the contiguous axis (rows; 45
+    rows leave the last packed pencil without a partner) and along strided axes (columns; partial last
+    tiles), for one field (ga_op_deriv) and for two time steps at once (the body force)."""
+    import paper_2510_08782_gb300 as ga
+
+    P, m0, _, v = _problem(shape, prec, model="advection", nt=4)
+    f = quantise(random_fourier_field(shape, 1, 6, np.random.default_rng(4))[0], prec)
+    ref = osp.grad(f)
+    for a in range(3):
+        out = empty(shape, prec)
+        ga.ga_op_deriv(P.ctx, P.dtype, to_dev(f, prec), a, out)
+        assert rel_l2(host(out), ref[a]) < TOL[prec], (a, rel_l2(host(out), ref[a]))
+    lam1 = quantise(random_fourier_field(shape, 1, 4, np.random.default_rng(5))[0], prec)
+    b = empty(v.shape, prec)
+    ga.ga_op_body_force(P.ctx, P.dtype, to_dev(v, prec), to_dev(lam1, prec), b)
+    ms = forward_states("advection", m0, v, 4, mu=osp.div(v))
+    ls = adjoint_states("advection", lam1, v, 4, mu=osp.div(v))
+    bref = np.zeros_like(v)
+    for j in range(5):
+        bref += 0.25 * (0.5 if j in (0, 4) else 1.0) * ls[j] * osp.grad(ms[j])
+    assert rel_l2(host(b), bref) < TOL[prec] * 3
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("s", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(32, 24), (16, 12, 20)])

@@ -85,3 +85,38 @@ def test_set_tiles_rejects_bad_shapes():
             ga_op_set_tiles(P.ctx, bad)
         assert e.value.status == 1
     assert ga_op_get_tiles(P.ctx, 3) == before
+
+
+@pytest.mark.parametrize("model", ["continuity", "advection"])
+@pytest.mark.parametrize("shape", [(40, 48, 64), (30, 16, 40)])
+def test_every_brick_depth_gives_identical_transport(shape, model):
+    """The brick depth of the FP32 3D transport steps (z voxels per thread) is chosen at setup by timing;
+    every depth gives bit-identical states, adjoint states and gradients, including a ragged last brick
+    along z (30 is no multiple of 4, 8 or 12)."""
+    from paper_2510_08782_gb300 import GaError, ga_op_adjoint, ga_op_forward, ga_op_get_sl_depth, ga_op_set_sl_depth
+
+    P, v, m0 = _problem(shape, "mixed", model=model)
+    assert ga_op_get_sl_depth(P.ctx) in (4, 8, 12)
+    vd = to_dev(v, "mixed")
+    lam1 = to_dev(np.random.default_rng(2).standard_normal(shape), "mixed")
+
+    def run():
+        st = empty((4,) + shape, "mixed")
+        ga_op_forward(P.ctx, P.dtype, vd, st)
+        la = empty((4,) + shape, "mixed")
+        ga_op_adjoint(P.ctx, P.dtype, vd, lam1, la)
+        g = empty((3,) + shape, "mixed")
+        obj = P.gradient(vd, g)
+        return [host(st), host(la), host(g), np.array([obj])]
+
+    outs = {}
+    for depth in (4, 8, 12):
+        ga_op_set_sl_depth(P.ctx, depth)
+        assert ga_op_get_sl_depth(P.ctx) == depth
+        outs[depth] = run()
+    for depth in (4, 12):
+        for x, y in zip(outs[depth], outs[8]):
+            assert np.array_equal(x, y)
+    with pytest.raises(GaError) as e:
+        ga_op_set_sl_depth(P.ctx, 5)
+    assert e.value.status == 1
