@@ -538,6 +538,149 @@ k_deriv_reg256(DerivIO<T> io, long long npen, long long S, long long outer_strid
   }
 }
 
+// FP32 form of the body force's two-step passes with their output operands staged: the two
+// multipliers and the accumulator are copied into shared memory with cp.async as the CTA starts, so all
+// of a tile's global reads are in flight while it transforms. The exchanges move the real and the
+// imaginary parts in two rounds through a float buffer (half the shared memory of a complex one), which
+// keeps three CTAs on an SM. Staging layouts: columns [n][c] (16 floats per row); rows [r][n] with a row
+// pitch of 272 floats, so the two pencils a warp covers fall on different banks. (The one-field passes
+// keep k_deriv_reg256: staging their single multiplier measured slower.)
+__device__ __forceinline__ void xchg_split(float2* a, float* xr, int x) {
+  // a[k] of this thread (fixed j = x) goes to entry (k, x); the thread then holds (x, q) for q = 0..15
+#pragma unroll
+  for (int k = 0; k < 16; ++k) xr[k * 17 + x] = a[k].x;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q].x = xr[x * 17 + q];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) xr[k * 17 + x] = a[k].y;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q].y = xr[x * 17 + q];
+}
+
+// reg256_deriv with the split exchanges (FP32).
+__device__ __forceinline__ void reg256_deriv_split(float2* a, const float2* tw, float* xr, int x) {
+  dft16<float>(a);
+#pragma unroll
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+  xchg_split(a, xr, x);  // thread holds k2 = x over q
+  dft16<float>(a);       // a[k1] = X[x + 16 k1]
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    const int k = x + 16 * k1;
+    const float kt = (k == 128) ? 0.f : (k < 128 ? float(k) : float(k - 256));
+    a[k1] = make_float2(-kt * a[k1].y, kt * a[k1].x);
+  }
+  idft16<float>(a);  // a[n1]
+#pragma unroll
+  for (int n1 = 1; n1 < 16; ++n1) a[n1] = cmul(a[n1], cconj(tw[n1 * x]));
+  __syncthreads();  // every thread has read the first exchange
+  xchg_split(a, xr, x);  // thread holds n1 = x over k2
+  idft16<float>(a);      // a[n2]: 256 times the derivative at x + 16 n2
+}
+
+template <bool ROWS> struct Reg256S {
+  static constexpr int PITCH = ROWS ? 272 : 16;
+  static constexpr int FIELD = ROWS ? 16 * PITCH : 256 * 16;  // floats of one staged field
+  static constexpr size_t bytes() { return sizeof(float) * (2 * 256 + 16 * kX16P + 3 * FIELD); }
+};
+
+template <bool ROWS>
+__global__ void __launch_bounds__(256, 3)
+k_deriv_pair256s(DerivIO<float> io, long long npen, long long S, long long outer_stride,
+                 const float2* __restrict__ twg, int vec) {
+  using Z = Reg256S<ROWS>;
+  constexpr int L = 256, PITCH = Z::PITCH, FIELD = Z::FIELD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float* xr = reinterpret_cast<float*>(tw + L);
+  float* stg = xr + 16 * kX16P;  // 16-byte aligned: 2 KB of twiddles + 16 * 273 floats
+  const int t = threadIdx.x;
+  const int p = ROWS ? (t >> 4) : (t & 15);
+  const int x = ROWS ? (t & 15) : (t >> 4);
+  // the tile: base offset and rows/columns present
+  long long base;
+  int valid;
+  if (ROWS) {
+    const long long r0 = (long long)blockIdx.x * 16;
+    base = r0 * L;
+    valid = (int)((npen - r0) < 16 ? (npen - r0) : 16);
+  } else {
+    const long long c0 = (long long)blockIdx.x * 16;
+    base = (long long)blockIdx.y * outer_stride + c0;
+    valid = (int)((npen - c0) < 16 ? (npen - c0) : 16);
+  }
+  const float* st_src[3] = {io.mult, io.mult2, io.accumulate ? io.out : nullptr};
+  const bool full = vec && valid == 16;
+#pragma unroll
+  for (int fi = 0; fi < 3; ++fi) {
+    const float* g = st_src[fi];
+    if (!g) continue;
+    float* d = stg + fi * FIELD;
+    if (ROWS) {
+      if (full) {
+        for (int c = t; c < 16 * (L / 4); c += 256) {
+          const int r = c >> 6, q = c & 63;
+          cpa16(d + r * PITCH + 4 * q, g + base + (long long)r * L + 4 * q);
+        }
+      } else {
+        for (int e = t; e < valid * L; e += 256) {
+          const int r = e >> 8, n = e & 255;
+          cpa_elem<float>(d + r * PITCH + n, g + base + (long long)r * L + n);
+        }
+      }
+    } else {
+      if (full) {
+        for (int c = t; c < L * 4; c += 256) {
+          const int n = c >> 2, q = c & 3;
+          cpa16(d + n * 16 + 4 * q, g + base + (long long)n * S + 4 * q);
+        }
+      } else {
+        for (int e = t; e < L * 16; e += 256) {
+          const int n = e >> 4, c = e & 15;
+          if (c < valid) cpa_elem<float>(d + n * 16 + c, g + base + (long long)n * S + c);
+        }
+      }
+    }
+  }
+  cpa_commit();
+  for (int i = t; i < L; i += blockDim.x) tw[i] = twg[i];
+  const bool v0 = p < valid;
+  const long long off = base + (ROWS ? (long long)p * L + x : p + (long long)x * S);
+  const long long st16 = ROWS ? 16 : 16 * S;
+  float2 a[16];
+  {
+    const float* fp = io.f + off;
+    const float* f2p = io.f2 + off;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      a[m] = v0 ? make_float2(fp[0], f2p[0]) : make_float2(0.f, 0.f);
+      fp += st16;
+      f2p += st16;
+    }
+  }
+  __syncthreads();  // twiddle table
+  reg256_deriv_split(a, tw, xr + p * kX16P, x);
+  cpa_wait<0>();
+  __syncthreads();
+  if (!v0) return;
+  const float inv = 1.f / 256.f;
+  long long e = off;
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2, e += st16) {
+    const int n = x + 16 * n2;
+    const int i = ROWS ? p * PITCH + n : n * 16 + p;
+    float w1 = io.coef * (a[n2].x * inv);
+    if (io.mult) w1 *= stg[i];
+    if (io.accumulate) w1 += stg[2 * FIELD + i];
+    float w2 = io.coef2 * (a[n2].y * inv);
+    if (io.mult2) w2 *= stg[FIELD + i];
+    io.out[e] = w2 + w1;
+  }
+}
+
 // ---- real-to-complex FFT of row pairs ---------------------------------------------------------
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
@@ -744,7 +887,45 @@ static cudaError_t deriv_pass(const Grid& g, const FftTables<T>& ft, int axis, c
     if (io.accumulate) return cudaSuccess;
     return cudaMemsetAsync(io.out, 0, sizeof(T) * g.nvox, st);
   }
-  if (L == kRegFftLen) {  // register-resident transform (k_deriv_reg256)
+  if constexpr (std::is_same<T, float>::value && PAIR) {
+    if (L == kRegFftLen) {  // register-resident transform with staged operands (k_deriv_pair256s)
+      const auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+      const bool ptrs16 = (!io.mult || al(io.mult)) && (!io.mult2 || al(io.mult2)) && (!io.accumulate || al(io.out));
+      if (axis == 2) {
+        const long long rows = (long long)g.n[0] * g.n[1];
+        auto kern = k_deriv_pair256s<true>;
+        constexpr size_t sm = Reg256S<true>::bytes();
+        cudaError_t e = allow_smem(kern, sm);
+        if (e != cudaSuccess) return e;
+        note_launches(1);
+        kern<<<(unsigned)((rows + 15) / 16), 256, sm, st>>>(io, rows, 1, 0, ft.tw[2], ptrs16 ? 1 : 0);
+        return cudaGetLastError();
+      }
+      const int nx = g.n[2];
+      long long S, outer_stride;
+      int outer;
+      if (axis == 1) {
+        S = nx;
+        outer = g.n[0];
+        outer_stride = (long long)g.n[1] * nx;
+      } else {
+        S = (long long)g.n[1] * nx;
+        outer = g.n[1];
+        outer_stride = nx;
+      }
+      auto kern = k_deriv_pair256s<false>;
+      constexpr size_t sm = Reg256S<false>::bytes();
+      cudaError_t e = allow_smem(kern, sm);
+      if (e != cudaSuccess) return e;
+      note_launches(1);
+      // 16-byte copies of column segments: rows of whole chunks (nx a multiple of 4)
+      const int vec = (ptrs16 && nx % 4 == 0) ? 1 : 0;
+      kern<<<dim3((unsigned)((nx + 15) / 16), (unsigned)outer), 256, sm, st>>>(io, nx, S, outer_stride, ft.tw[axis],
+                                                                                 vec);
+      return cudaGetLastError();
+    }
+  }
+  if (L == kRegFftLen) {  // register-resident transform (k_deriv_reg256: FP64, and the one-field FP32 passes)
     const size_t sm = sizeof(cx<T>) * (256 + 16 * kX16P);
     constexpr int rp = PAIR ? 1 : 2;
     if (axis == 2) {
