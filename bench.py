@@ -47,9 +47,9 @@ REF_SAMPLE_N = 48  # oracle sample grid of each step of the reference arm
 PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ, PROF_DERIV_PAIR = 0, 1, 2, 3, 4
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sl_tile2<1> launch from an ncu
-# capture of this benchmark at 192^3 (143.4 MB read + 16.7 MB written, mean of 3 launches), scaled to
-# n^3 by the voxel count. Valid for the kernel as captured; set to None when it changes.
-SL_FWD_TRAFFIC_192 = 160.1e6
+# capture of this benchmark at 192^3, scaled to n^3 by the voxel count. Valid for the kernel as
+# captured; None while the kernel has changed since the last capture.
+SL_FWD_TRAFFIC_192 = None
 
 
 def peaks():

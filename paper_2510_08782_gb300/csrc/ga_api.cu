@@ -98,6 +98,9 @@ template <typename T> struct Engine : EngineBase {
   cudaStream_t st;
   FftTables<T> ft;
   cx<T>* twd[3] = {nullptr, nullptr, nullptr};  // the device twiddle tables ft.tw points at
+  cx<T>* qp[2] = {nullptr, nullptr};            // (pi, pi mu) pairs of the continuity state chain
+  const T* q_src = nullptr;
+  int q_idx = 0;
   std::vector<void*> allocs;
   void* pinned = nullptr;
   double* hres = nullptr;
@@ -245,6 +248,10 @@ template <typename T> struct Engine : EngineBase {
     }
     al(dM, (long long)W1 * W1);
     al(dbeta, (long long)kMaxWin + 4);
+    if (std::is_same<T, float>::value && dim == 3 && model == GA_MODEL_CONTINUITY) {
+      al(qp[0], nv);
+      al(qp[1], nv);
+    }
   }
 
   void init(ga_ctx* c, const void* hm0, const void* hm1, int mem) {
@@ -361,6 +368,7 @@ template <typename T> struct Engine : EngineBase {
       int choice = 0;
       for (int zb : kSlDepths) {
         g.sl_bz = zb;
+        chain_reset();
         sl_forward(m0, tmp[0]);  // loads the kernels
         sl_adjoint(m1, tmp[1]);
         ck(cudaEventRecord(ev[0], st), "event");
@@ -417,9 +425,27 @@ template <typename T> struct Engine : EngineBase {
   }
   bool stored(int j) const { return K == 0 || j % K == 0 || j == nt; }
 
+  // One state step. Continuity steps of FP32 3D grids also write the pairs (pi_{j+1}, pi_{j+1} mu) into
+  // one of two chain buffers qp, and a step whose input is the previous step's output stages those pairs
+  // as they are (no interleaving pass). q_src names the state whose pairs qp[q_idx] holds; every chain
+  // of steps starts with chain_reset(), so a chain never reads pairs of a state it did not write.
+  void chain_reset() {
+    q_src = nullptr;
+    q_idx = 0;
+  }
   void sl_forward(const T* src, T* dst) {
+    cx<T>* qin = nullptr;
+    cx<T>* qout = nullptr;
+    if (qp[0]) {
+      if (src != nullptr && src == q_src) {
+        qin = qp[q_idx];
+        q_idx ^= 1;
+      }
+      qout = qp[q_idx];
+      q_src = dst;
+    }
     prof_begin(PROF_SL_FWD);
-    ck(launch_sl_forward<T>(g, model == GA_MODEL_CONTINUITY, src, xm, mu, dst, (T)ht, st), "sl_forward");
+    ck(launch_sl_forward<T>(g, model == GA_MODEL_CONTINUITY, src, xm, mu, dst, (T)ht, st, qin, qout), "sl_forward");
     prof_end(PROF_SL_FWD);
   }
   void sl_adjoint(const T* src, T* dst) {
@@ -492,6 +518,7 @@ template <typename T> struct Engine : EngineBase {
   // State solve keeping only the final state; returns pointer to m(1).
   const T* forward_final(const T* v) {
     ck(launch_departure<T>(g, v, xm, xp, (T)ht, st, /*both=*/0), "departure");
+    chain_reset();
     const T* cur = m0;
     for (int j = 0; j < nt; ++j) {
       T* dst = tmp[(j + 1) & 1];
@@ -511,6 +538,7 @@ template <typename T> struct Engine : EngineBase {
   // segment buffer, where the backward sweep, which starts there, finds them: that segment is never
   // recomputed.
   void forward_all() {
+    chain_reset();
     const T* cur = m0;
     const int jl = last_segment();
     for (int j = 0; j < nt; ++j) {
@@ -528,6 +556,7 @@ template <typename T> struct Engine : EngineBase {
     if (stored(j)) return slot(j);
     const int js = (j / K) * K;
     if (seg_base != js) {
+      chain_reset();
       const T* cur = slot(js);
       const int last = (js + K - 1 < nt - 1) ? js + K - 1 : nt - 1;
       for (int i = js + 1; i <= last; ++i) {
@@ -1826,6 +1855,7 @@ ga_status ga_op_forward(ga_ctx* ctx, const void* v, void* states) {
     e.compute_mu(vv);
     e.ck(launch_departure<T>(e.g, vv, e.xm, e.xp, (T)e.ht, e.st), "departure");
     e.ck(cudaMemcpyAsync(out, e.m0, sizeof(T) * e.nv, cudaMemcpyDeviceToDevice, e.st), "copy");
+    e.chain_reset();
     for (int j = 0; j < e.nt; ++j) e.sl_forward(out + (long long)j * e.nv, out + (long long)(j + 1) * e.nv);
     e.ck(cudaStreamSynchronize(e.st), "sync");
   });

@@ -76,13 +76,17 @@ template <typename T>
 cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cudaStream_t st, int both = 1);
 cudaError_t launch_departure_tile(const Grid& g, const float* v, float* xm, float* xp, float ht, int both,
                                   cudaStream_t st);
-// One state step m_{j+1} = I[m_j](X-) (continuity: with the RK2 source of -pi div v).
+// One state step m_{j+1} = I[m_j](X-) (continuity: with the RK2 source of -pi div v). For the two-field
+// steps of FP32 3D grids (continuity state, advection adjoint), qout (optional) receives the pairs
+// (m_{j+1}, m_{j+1} mu) of the output, and qin (optional) gives the same pairs of the input, which the
+// step then stages as they are instead of m and mu.
 template <typename T>
 cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T* xm, const T* mu,
-                              T* out, T ht, cudaStream_t st);
+                              T* out, T ht, cudaStream_t st, const cx<T>* qin = nullptr, cx<T>* qout = nullptr);
 // Tiled FP32 3D state (adjoint = 0) or adjoint (adjoint = 1) step (sl_tile_kernels.cu).
 cudaError_t launch_sl_tile(const Grid& g, int adjoint, int continuity, const float* f, const float* disp,
-                           const float* mu, float* out, float ht, cudaStream_t st);
+                           const float* mu, float* out, float ht, cudaStream_t st, const float2* qin = nullptr,
+                           float2* qout = nullptr);
 // One adjoint step lambda_j from lambda_{j+1} (advection: with the source lambda div v).
 template <typename T>
 cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const T* xp, const T* mu,

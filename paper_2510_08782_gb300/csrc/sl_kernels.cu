@@ -202,9 +202,9 @@ cudaError_t launch_departure(const Grid& g, const T* v, T* xm, T* xp, T ht, cuda
 
 template <typename T>
 cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T* xm, const T* mu, T* out,
-                              T ht, cudaStream_t st) {
+                              T ht, cudaStream_t st, const cx<T>* qin, cx<T>* qout) {
   if constexpr (std::is_same<T, float>::value) {
-    if (g.dim == 3) return launch_sl_tile(g, 0, continuity, m, xm, mu, out, ht, st);
+    if (g.dim == 3) return launch_sl_tile(g, 0, continuity, m, xm, mu, out, ht, st, qin, qout);
   }
   const unsigned gr = grid_for(g.nvox);
   if (g.dim == 3) {
@@ -261,7 +261,7 @@ cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const
 #define GA_INST(T)                                                                                  \
   template cudaError_t launch_departure<T>(const Grid&, const T*, T*, T*, T, cudaStream_t, int);    \
   template cudaError_t launch_sl_forward<T>(const Grid&, int, const T*, const T*, const T*, T*, T,    \
-                                            cudaStream_t);                                           \
+                                            cudaStream_t, const cx<T>*, cx<T>*);                                           \
   template cudaError_t launch_sl_adjoint<T>(const Grid&, int, const T*, const T*, const T*, T*, T,    \
                                             cudaStream_t);
 GA_INST(float)

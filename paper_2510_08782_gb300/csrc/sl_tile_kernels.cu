@@ -82,8 +82,11 @@ template <int MODE> __device__ __forceinline__ float step_value(float P, float S
 
 template <int MODE>
 __device__ __forceinline__ void store_step(float* __restrict__ out, const float* __restrict__ mu, long long idx,
-                                           float P, float S, float ht) {
-  out[idx] = step_value<MODE>(P, S, (MODE == 1 || MODE == 2) ? mu[idx] : 0.f, ht);
+                                           float P, float S, float ht, float2* __restrict__ qout) {
+  const float m = (MODE == 1 || MODE == 2) ? mu[idx] : 0.f;
+  const float y = step_value<MODE>(P, S, m, ht);
+  out[idx] = y;
+  if ((MODE == 1 || MODE == 2) && qout) qout[idx] = make_float2(y, y * m);
 }
 
 // ---- asynchronous global -> shared copies (LDGSTS) ----
@@ -154,6 +157,40 @@ __device__ __forceinline__ void stage_async(float* dst, const float* __restrict_
   }
 }
 
+// Issue the copies of one brick's tile of (f, f mu) pairs from `src` into the pair layout (row pitch TXP)
+// at `dst` (all threads of the CTA): the two-field steps' tile without the interleaving pass.
+__device__ __forceinline__ void cp_async8(float2* sdst, const float2* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc));
+}
+template <int ZB>
+__device__ __forceinline__ void stage_pairs_async(float2* dst, const float2* __restrict__ src, const BrickIdx& bi,
+                                                  int n0, int n1, int n2, bool vec) {
+  constexpr int TZ = Tile<ZB>::TZ;
+  const int gx0 = bi.bx * BX - XOFF, gy0 = bi.by * BY - H - 1, gz0 = bi.bz * ZB - H - 1;
+  if (vec) {  // 16-byte chunks of two pairs: n2 % 4 == 0 and n2 >= TXA (see stage_async)
+    for (int c = threadIdx.x; c < TY * TZ * (TXA / 2); c += blockDim.x) {
+      const int cx = c % (TXA / 2), row = c / (TXA / 2);
+      const int ty = row % TY, tz = row / TY;
+      int gy = gy0 + ty, gz = gz0 + tz;
+      gy = gy < 0 ? gy + n1 : (gy >= n1 ? gy - n1 : gy);
+      gz = gz < 0 ? gz + n0 : (gz >= n0 ? gz - n0 : gz);
+      int gx = gx0 + 2 * cx;
+      gx = gx < 0 ? gx + n2 : (gx >= n2 ? gx - n2 : gx);
+      cp_async16(reinterpret_cast<float*>(dst + row * TXP + 2 * cx), reinterpret_cast<const float*>(
+                                                                          src + ((size_t)gz * n1 + gy) * n2 + gx));
+    }
+  } else {
+    for (int e = threadIdx.x; e < TXA * TY * TZ; e += blockDim.x) {
+      const int tx = e % TXA, row = e / TXA;
+      const int ty = row % TY, tz = row / TY;
+      const int gy = wrap_any(gy0 + ty, n1), gz = wrap_any(gz0 + tz, n0);
+      const int gx = wrap_any(gx0 + tx, n2);
+      cp_async8(dst + row * TXP + tx, src + ((size_t)gz * n1 + gy) * n2 + gx);
+    }
+  }
+}
+
 // ---- scalar / packed-pair arithmetic with explicit rounding ----
 // The pair type float2 runs two independent lanes through the FP32x2 FMA path of sm_100+; the scalar
 // overloads perform the same operations in the same order, so a voxel's interpolant does not depend
@@ -210,7 +247,7 @@ __device__ __forceinline__ bool in_halo(float fz, float fy, float fx) {
 // halo, global taps otherwise. Two-field steps read the interleaved (f, f mu) tile `sf`.
 template <int MODE>
 __device__ __forceinline__ void sl_single(const float* __restrict__ f, const float* __restrict__ mu,
-                                          float* __restrict__ out, const float* sf, int col,
+                                          float* __restrict__ out, float2* __restrict__ qout, const float* sf, int col,
                                           long long idx, int gz, int v, int gy, int gx, float vz, float vy, float vx,
                                           int n0, int n1, int n2, float ht) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
@@ -232,7 +269,7 @@ __device__ __forceinline__ void sl_single(const float* __restrict__ f, const flo
   } else {
     gather_global<NF>(f, mu, gz, gy, gx, vz, vy, vx, n0, n1, n2, P, S);
   }
-  store_step<MODE>(out, mu, idx, P, S, ht);
+  store_step<MODE>(out, mu, idx, P, S, ht, qout);
 }
 
 // MODE 0: advection state step          out = I[f](X-)
@@ -248,7 +285,8 @@ __device__ __forceinline__ void sl_single(const float* __restrict__ f, const flo
 template <int MODE, int ZB>
 __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const float* __restrict__ mu,
                                              const float* __restrict__ disp, float* __restrict__ out, int n0, int n1,
-                                             int n2, float ht, int vec) {
+                                             int n2, float ht, int vec, const float2* __restrict__ qin,
+                                             float2* __restrict__ qout) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;  // staged fields: f (and f * mu)
   constexpr int TILEA = Tile<ZB>::A;
   extern __shared__ __align__(16) float smem[];
@@ -258,8 +296,13 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
   const long long plane = (long long)n1 * n2;
   const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
   const BrickIdx bi = brick_of(blockIdx.x, nbx, nby);
-  stage_async<ZB>(smem, f, bi, n0, n1, n2, vec != 0);
-  if (NF == 2) stage_async<ZB>(smem + TILEA, mu, bi, n0, n1, n2, vec != 0);
+  const bool pairs_in = NF == 2 && qin != nullptr;  // the previous step wrote (f, f mu): stage them as they are
+  if (pairs_in) {
+    stage_pairs_async<ZB>(reinterpret_cast<float2*>(smem), qin, bi, n0, n1, n2, vec != 0);
+  } else {
+    stage_async<ZB>(smem, f, bi, n0, n1, n2, vec != 0);
+    if (NF == 2) stage_async<ZB>(smem + TILEA, mu, bi, n0, n1, n2, vec != 0);
+  }
   cp_async_commit();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gx = bi.bx * BX + lane, gy = bi.by * BY + warp;
@@ -290,7 +333,9 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
   }
   asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
-  if (NF == 2) {
+  if (pairs_in) {
+    if (active && nz >= 2) fetch(0);
+  } else if (NF == 2) {
     // Interleave in place: the f and mu tiles (TILEA floats each) become TILEA pairs (f, f mu) over the
     // same bytes, so a tap of both fields is one 64-bit shared load. Every thread holds its elements
     // in registers across the barrier, since a pair overwrites other threads' source elements.
@@ -338,12 +383,16 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
         lagrange4v(vsplat<float2>(cya - fya), wy);
         lagrange4v(vsplat<float2>(cxa - fxa), wx);
         const float2 A = interp64<TXP, float2>(wz, wy, wx, [&](int o) { return sp[ba + o]; });
-        out[ia] = step_value<MODE>(A.x, A.y, cma, ht);
+        const float ya = step_value<MODE>(A.x, A.y, cma, ht);
+        out[ia] = ya;
+        if (qout) qout[ia] = make_float2(ya, ya * cma);
         lagrange4v(vsplat<float2>(czb - fzb), wz);
         lagrange4v(vsplat<float2>(cyb - fyb), wy);
         lagrange4v(vsplat<float2>(cxb - fxb), wx);
         const float2 B = interp64<TXP, float2>(wz, wy, wx, [&](int o) { return sp[bb + o]; });
-        out[ib] = step_value<MODE>(B.x, B.y, cmb, ht);
+        const float yb = step_value<MODE>(B.x, B.y, cmb, ht);
+        out[ib] = yb;
+        if (qout) qout[ib] = make_float2(yb, yb * cmb);
       } else {  // one field: the pair of voxels as one packed pair
         lagrange4v(make_float2(cza - fza, czb - fzb), wz);
         lagrange4v(make_float2(cya - fya, cyb - fyb), wy);
@@ -353,13 +402,13 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
         out[ib] = step_value<MODE>(P.y, 0.f, cmb, ht);
       }
     } else {
-      sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * ZB + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
-      sl_single<MODE>(f, mu, out, sf, col, ib, bi.bz * ZB + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
+      sl_single<MODE>(f, mu, out, qout, sf, col, ia, bi.bz * ZB + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
+      sl_single<MODE>(f, mu, out, qout, sf, col, ib, bi.bz * ZB + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
     }
   }
   if (v < nz) {
     const long long ia = idx0 + v * plane;
-    sl_single<MODE>(f, mu, out, sf, col, ia, bi.bz * ZB + v, v, gy, gx, disp[ia], disp[nv + ia], disp[2 * nv + ia],
+    sl_single<MODE>(f, mu, out, qout, sf, col, ia, bi.bz * ZB + v, v, gy, gx, disp[ia], disp[nv + ia], disp[2 * nv + ia],
                     n0, n1, n2, ht);
   }
 }
@@ -474,14 +523,16 @@ __global__ void __launch_bounds__(256, ZB <= 8 ? 3 : 2) k_sl_tile2(const float* 
                                                                   const float* __restrict__ mu,
                                                                   const float* __restrict__ disp,
                                                                   float* __restrict__ out, int n0, int n1, int n2,
-                                                                  float ht, int vec) {
-  sl_tile_body<MODE, ZB>(f, mu, disp, out, n0, n1, n2, ht, vec);
+                                                                  float ht, int vec, const float2* __restrict__ qin,
+                                                                  float2* __restrict__ qout) {
+  sl_tile_body<MODE, ZB>(f, mu, disp, out, n0, n1, n2, ht, vec, qin, qout);
 }
 template <int MODE, int ZB>
 __global__ void __launch_bounds__(256, 4) k_sl_tile1(const float* __restrict__ f, const float* __restrict__ mu,
                                                      const float* __restrict__ disp, float* __restrict__ out, int n0,
-                                                     int n1, int n2, float ht, int vec) {
-  sl_tile_body<MODE, ZB>(f, mu, disp, out, n0, n1, n2, ht, vec);
+                                                     int n1, int n2, float ht, int vec, const float2* __restrict__ qin,
+                                                     float2* __restrict__ qout) {
+  sl_tile_body<MODE, ZB>(f, mu, disp, out, n0, n1, n2, ht, vec, qin, qout);
 }
 
 // RK2 departure points (displacements in cells) for 3D FP32 grids: X* = x -/+ h_t v(x), then
@@ -605,12 +656,12 @@ k_departure_tile(const float* __restrict__ v, float* __restrict__ xm, float* __r
 
 template <int MODE, int ZB>
 cudaError_t launch_mode_zb(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
-                           cudaStream_t st) {
+                           const float2* qin, float2* qout, cudaStream_t st) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
   constexpr int TILEA = Tile<ZB>::A, TILEP = Tile<ZB>::P;
   // two-field steps: the f and mu tiles, then the same bytes (plus row padding) as (f, f mu) pairs
   const size_t sm = NF == 2 ? sizeof(float) * (2 * TILEP > 2 * TILEA ? 2 * TILEP : 2 * TILEA) : sizeof(float) * TILEA;
-  void (*kern)(const float*, const float*, const float*, float*, int, int, int, float, int);
+  void (*kern)(const float*, const float*, const float*, float*, int, int, int, float, int, const float2*, float2*);
   if constexpr (NF == 2) kern = k_sl_tile2<MODE, ZB>;
   else kern = k_sl_tile1<MODE, ZB>;
   static std::atomic<bool> attr{false};
@@ -622,21 +673,24 @@ cudaError_t launch_mode_zb(const Grid& g, const float* f, const float* mu, const
   const int nb = ((g.n[2] + BX - 1) / BX) * ((g.n[1] + BY - 1) / BY) * ((g.n[0] + ZB - 1) / ZB);
   // 16-byte copies need n2 % 4 == 0 (rows of whole chunks), no chunk across the periodic seam
   // (n2 >= TXA) and 16-byte aligned field pointers
-  const bool aligned = ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(mu ? mu : f)) & 15u) == 0;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(mu ? mu : f) |
+                         reinterpret_cast<uintptr_t>(qin ? qin : reinterpret_cast<const float2*>(f))) &
+                        15u) == 0;
   const int vec = (g.n[2] % 4 == 0 && g.n[2] >= TXA && g.n[1] >= TY && g.n[0] >= Tile<ZB>::TZ && aligned) ? 1 : 0;
   note_launches(1);
-  kern<<<nb, kTileThreads, sm, st>>>(f, mu, disp, out, g.n[0], g.n[1], g.n[2], ht, vec);
+  kern<<<nb, kTileThreads, sm, st>>>(f, mu, disp, out, g.n[0], g.n[1], g.n[2], ht, vec, NF == 2 ? qin : nullptr,
+                                     NF == 2 ? qout : nullptr);
   return cudaGetLastError();
 }
 
 // Brick depths the setup autotuner chooses from (Grid::sl_bz); every depth gives the same values.
 template <int MODE>
 cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
-                        cudaStream_t st) {
+                        const float2* qin, float2* qout, cudaStream_t st) {
   switch (g.sl_bz) {
-    case 4: return launch_mode_zb<MODE, 4>(g, f, mu, disp, out, ht, st);
-    case 12: return launch_mode_zb<MODE, 12>(g, f, mu, disp, out, ht, st);
-    default: return launch_mode_zb<MODE, 8>(g, f, mu, disp, out, ht, st);
+    case 4: return launch_mode_zb<MODE, 4>(g, f, mu, disp, out, ht, qin, qout, st);
+    case 12: return launch_mode_zb<MODE, 12>(g, f, mu, disp, out, ht, qin, qout, st);
+    default: return launch_mode_zb<MODE, 8>(g, f, mu, disp, out, ht, qin, qout, st);
   }
 }
 
@@ -660,11 +714,13 @@ cudaError_t launch_departure_tile(const Grid& g, const float* v, float* xm, floa
 }
 
 cudaError_t launch_sl_tile(const Grid& g, int adjoint, int continuity, const float* f, const float* disp,
-                           const float* mu, float* out, float ht, cudaStream_t st) {
+                           const float* mu, float* out, float ht, cudaStream_t st, const float2* qin, float2* qout) {
   if (!adjoint) {
-    return continuity ? launch_mode<1>(g, f, mu, disp, out, ht, st) : launch_mode<0>(g, f, mu, disp, out, ht, st);
+    return continuity ? launch_mode<1>(g, f, mu, disp, out, ht, qin, qout, st)
+                      : launch_mode<0>(g, f, mu, disp, out, ht, qin, qout, st);
   }
-  return continuity ? launch_mode<3>(g, f, mu, disp, out, ht, st) : launch_mode<2>(g, f, mu, disp, out, ht, st);
+  return continuity ? launch_mode<3>(g, f, mu, disp, out, ht, qin, qout, st)
+                    : launch_mode<2>(g, f, mu, disp, out, ht, qin, qout, st);
 }
 
 }  // namespace ga
