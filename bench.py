@@ -47,9 +47,11 @@ REF_SAMPLE_N = 48  # oracle sample grid of each step of the reference arm
 PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ, PROF_DERIV_PAIR = 0, 1, 2, 3, 4
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sl_tile2<1> launch from an ncu
-# capture of this benchmark at 192^3, scaled to n^3 by the voxel count. Valid for the kernel as
-# captured; None while the kernel has changed since the last capture.
-SL_FWD_TRAFFIC_192 = None
+# capture of this benchmark at 192^3 (chained state steps at brick depth 12: 171.7 MB read + 57.9 MB
+# written, mean of 3 launches), scaled to n^3 by the voxel count. Valid for the kernel as captured, at
+# that brick depth; None while the kernel has changed since the last capture.
+SL_FWD_TRAFFIC_192 = 229.6e6
+SL_FWD_TRAFFIC_DEPTH = 12
 
 
 def peaks():
@@ -620,14 +622,14 @@ def main():
     per_launch_ms = prof_ms / max(prof_n, 1)
     bytes_per_launch = algo[1] * nv
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
-    sl_depth = ga.ga_op_get_sl_depth(P.ctx)  # brick depth of the transport steps chosen at setup
+    sl_depth = ga.ga_op_get_sl_depth(P.ctx)  # brick depths (state, adjoint steps) chosen at setup
     traffic = None
-    if args.prof_class == PROF_SL_FWD and SL_FWD_TRAFFIC_192 is not None and sl_depth == 8:
+    if args.prof_class == PROF_SL_FWD and SL_FWD_TRAFFIC_192 is not None and sl_depth[0] == SL_FWD_TRAFFIC_DEPTH:
         traffic = round(SL_FWD_TRAFFIC_192 * nv / 192.0 ** 3)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "traffic_note": "bytes per launch from an ncu capture at 192^3 (brick depth 8) scaled by voxel "
-                                "count; null for another brick depth",
+                "traffic_note": "bytes per launch of the chained state step from an ncu capture at 192^3 "
+                                "(brick depth 12) scaled by voxel count; null for another brick depth",
                 "kernel": algo[0],
                 "bytes_per_launch": bytes_per_launch, "launches": prof_n, "mean_launch_ms": per_launch_ms,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"}
@@ -882,7 +884,7 @@ def main():
                            "l2": "inputs larger than L2: each 256^3 field is 64 MiB and a step touches GBs",
                            "parallelism": "replicas (one independent problem per GPU)" if ws > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-                "deriv_tiles_zyx": deriv_tiles, "sl_brick_depth": sl_depth,
+                "deriv_tiles_zyx": deriv_tiles, "sl_brick_depth_state_adjoint": list(sl_depth),
                 "clocks": clocks, "tts": tts, "tts_device": tts_dev, "fp64_tts": fp64, "batch": batch,
                 "methods_tts": methods, "deformation": deformation, "dto": dto_res, "grad_only_evals_per_s": grad_only,
                 "grad_evals_in_timed_steps": grad_evals, "last_step": {k: step_stats[k] for k in

@@ -53,15 +53,15 @@ ga_status ga_op_deriv(ga_ctx* ctx, const void* f, int axis, void* df);
 ga_status ga_op_get_tiles(const ga_ctx* ctx, int* pencils);
 ga_status ga_op_set_tiles(ga_ctx* ctx, const int* pencils);
 
-/* Brick depth of the FP32 3D semi-Lagrangian transport steps (Sec. 2.2): the number of z voxels each
- * thread of a 32 x 8 x depth brick interpolates from the brick's staged tile (4, 8 or 12). ga_setup picks
- * it by timing one state step and one adjoint step of the context's model at every depth on its own
- * grid (cached per grid and model for the process); every depth gives the same values bit for bit.
- * ga_op_set_sl_depth overrides it (0 restores 8; GA_ERR_ARG for any other value than 4, 8, 12). FP64
- * and 2D contexts keep 8 (their steps are not tiled). CUDA graphs the context recorded earlier keep the
- * depth they were recorded with. */
-ga_status ga_op_get_sl_depth(const ga_ctx* ctx, int* depth);
-ga_status ga_op_set_sl_depth(ga_ctx* ctx, int depth);
+/* Brick depths of the FP32 3D semi-Lagrangian transport steps (Sec. 2.2): the number of z voxels each
+ * thread of a 32 x 8 x depth brick interpolates from the brick's staged tile (4, 8 or 12), one for the
+ * state steps and one for the adjoint steps. ga_setup picks each by timing its steps at every depth on
+ * the context's own grid (state steps chained as in a sweep; cached per grid and model for the
+ * process); every depth gives the same values bit for bit. ga_op_set_sl_depth overrides them (0
+ * restores 8; GA_ERR_ARG for any value other than 0, 4, 8, 12). FP64 and 2D contexts keep 8 (their steps
+ * are not tiled). CUDA graphs the context recorded earlier keep the depths they were recorded with. */
+ga_status ga_op_get_sl_depth(const ga_ctx* ctx, int* state_depth, int* adjoint_depth);
+ga_status ga_op_set_sl_depth(ga_ctx* ctx, int state_depth, int adjoint_depth);
 
 /* Spectral divergence mu = sum_c d_c v_c. */
 ga_status ga_op_div(ga_ctx* ctx, const void* v, void* mu);

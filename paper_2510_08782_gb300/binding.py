@@ -84,8 +84,8 @@ _SIGS = {
     "ga_op_div": ([_vp, _vp, _vp], _c_int),
     "ga_op_get_tiles": ([_vp, ctypes.POINTER(_c_int)], _c_int),
     "ga_op_set_tiles": ([_vp, ctypes.POINTER(_c_int)], _c_int),
-    "ga_op_get_sl_depth": ([_vp, ctypes.POINTER(_c_int)], _c_int),
-    "ga_op_set_sl_depth": ([_vp, _c_int], _c_int),
+    "ga_op_get_sl_depth": ([_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)], _c_int),
+    "ga_op_set_sl_depth": ([_vp, _c_int, _c_int], _c_int),
     "ga_op_fft_r2c": ([_vp, _vp, _vp], _c_int),
     "ga_op_fft_c2r": ([_vp, _vp, _vp], _c_int),
     "ga_op_apply_L": ([_vp, _vp, _vp], _c_int),
@@ -402,14 +402,17 @@ def ga_op_get_tiles(ctx, dim):
 
 
 def ga_op_get_sl_depth(ctx):
-    """Brick depth (z voxels per thread) of the FP32 3D transport steps chosen by the autotuner."""
-    d = _c_int()
-    _check(lib().ga_op_get_sl_depth(ctx, ctypes.byref(d)), ctx)
-    return d.value
+    """Brick depths (z voxels per thread) of the FP32 3D state and adjoint steps chosen by the autotuner:
+    (state_depth, adjoint_depth)."""
+    a, b = _c_int(), _c_int()
+    _check(lib().ga_op_get_sl_depth(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
 
 
-def ga_op_set_sl_depth(ctx, depth):
-    _check(lib().ga_op_set_sl_depth(ctx, int(depth)), ctx)
+def ga_op_set_sl_depth(ctx, state_depth, adjoint_depth=None):
+    """Set both depths (adjoint_depth defaults to state_depth); 0 restores 8."""
+    b = state_depth if adjoint_depth is None else adjoint_depth
+    _check(lib().ga_op_set_sl_depth(ctx, int(state_depth), int(b)), ctx)
 
 
 def ga_op_set_tiles(ctx, pencils):

@@ -39,7 +39,8 @@ struct Grid {
   int n2h;                // n[2] / 2 + 1 (half spectrum along the contiguous axis)
   long long nvox;         // n0 * n1 * n2
   long long nhalf;        // n0 * n1 * n2h
-  int sl_bz = 8;          // brick depth (z voxels per thread) of the FP32 3D transport steps
+  int sl_bz = 8;          // brick depth (z voxels per thread) of the FP32 3D state steps
+  int sl_bz_adj = 8;      // the same for the adjoint steps
   GA_HD int axis_of(int c) const { return 3 - dim + c; }
 };
 

@@ -307,7 +307,7 @@ template <typename T> struct Engine : EngineBase {
   // result depends on the choice.
   void autotune_tiles() {
     static std::mutex mu;
-    static std::map<std::vector<int>, std::array<int, 7>> cache;
+    static std::map<std::vector<int>, std::array<int, 8>> cache;
     const std::vector<int> key = {(int)sizeof(T), g.n[0], g.n[1], g.n[2], model};
     {
       std::lock_guard<std::mutex> lk(mu);
@@ -318,10 +318,11 @@ template <typename T> struct Engine : EngineBase {
           ft.pair_pencils[a] = it->second[3 + a];
         }
         g.sl_bz = it->second[6];
+        g.sl_bz_adj = it->second[7];
         return;
       }
     }
-    std::array<int, 7> best = {0, 0, 0, 0, 0, 0, 8};
+    std::array<int, 8> best = {0, 0, 0, 0, 0, 0, 8, 8};
     for (int pair = 0; pair < 2; ++pair) {
       for (int a = 3 - dim; a < 3; ++a) {
         const int L = g.n[a];
@@ -358,35 +359,51 @@ template <typename T> struct Engine : EngineBase {
         best[3 * pair + a] = choice;
       }
     }
-    // Brick depth of the FP32 3D transport steps: one state and one adjoint step of this model per
-    // candidate, at zero displacement (the shared-memory gather every in-halo voxel takes).
+    // Brick depths of the FP32 3D transport steps, at zero displacement (the shared-memory gather every
+    // in-halo voxel takes): for the state steps, chained steps of this model (a step fed by the previous
+    // one, as in a sweep); for the adjoint steps, adjoint steps. The two are chosen separately.
     if (std::is_same<T, float>::value && dim == 3) {
       ck(cudaMemsetAsync(xm, 0, sizeof(T) * vl, st), "memset");
       ck(cudaMemsetAsync(xp, 0, sizeof(T) * vl, st), "memset");
       ck(cudaMemsetAsync(this->mu, 0, sizeof(T) * nv, st), "memset");
-      float best_ms = 0.f;
-      int choice = 0;
-      for (int zb : kSlDepths) {
-        g.sl_bz = zb;
-        chain_reset();
-        sl_forward(m0, tmp[0]);  // loads the kernels
-        sl_adjoint(m1, tmp[1]);
+      auto timed = [&](auto&& run) {
+        run();  // loads the kernels
         ck(cudaEventRecord(ev[0], st), "event");
-        for (int r = 0; r < 2; ++r) {
-          sl_forward(m0, tmp[0]);
-          sl_adjoint(m1, tmp[1]);
-        }
+        for (int r = 0; r < 3; ++r) run();
         ck(cudaEventRecord(ev[1], st), "event");
         ck(cudaEventSynchronize(ev[1]), "event sync");
         float ms = 0.f;
         ck(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
-        if (choice == 0 || ms < best_ms) {
-          choice = zb;
-          best_ms = ms;
+        return ms;
+      };
+      float best_f = 0.f, best_a = 0.f;
+      int choice_f = 0, choice_a = 0;
+      for (int zb : kSlDepths) {
+        g.sl_bz = zb;
+        chain_reset();
+        sl_forward(m0, tmp[0]);
+        const float mf = timed([&] {
+          sl_forward(tmp[0], tmp[1]);
+          sl_forward(tmp[1], tmp[0]);
+        });
+        if (choice_f == 0 || mf < best_f) {
+          choice_f = zb;
+          best_f = mf;
+        }
+        g.sl_bz_adj = zb;
+        const float ma = timed([&] {
+          sl_adjoint(m1, tmp[1]);
+          sl_adjoint(m0, tmp[1]);
+        });
+        if (choice_a == 0 || ma < best_a) {
+          choice_a = zb;
+          best_a = ma;
         }
       }
-      g.sl_bz = choice;
-      best[6] = choice;
+      g.sl_bz = choice_f;
+      g.sl_bz_adj = choice_a;
+      best[6] = choice_f;
+      best[7] = choice_a;
     }
     std::lock_guard<std::mutex> lk(mu);
     cache.emplace(key, best);
@@ -1919,23 +1936,28 @@ ga_status ga_op_get_tiles(const ga_ctx* ctx, int* pencils) {
   return GA_OK;
 }
 
-ga_status ga_op_get_sl_depth(const ga_ctx* ctx, int* depth) {
-  if (!ctx || !depth) return GA_ERR_ARG;
-  *depth = ctx->ef ? ctx->ef->g.sl_bz : ctx->ed->g.sl_bz;
+ga_status ga_op_get_sl_depth(const ga_ctx* ctx, int* state_depth, int* adjoint_depth) {
+  if (!ctx || !state_depth || !adjoint_depth) return GA_ERR_ARG;
+  const ga::Grid& g = ctx->ef ? ctx->ef->g : ctx->ed->g;
+  *state_depth = g.sl_bz;
+  *adjoint_depth = g.sl_bz_adj;
   return GA_OK;
 }
 
-ga_status ga_op_set_sl_depth(ga_ctx* ctx, int depth) {
+ga_status ga_op_set_sl_depth(ga_ctx* ctx, int state_depth, int adjoint_depth) {
   if (!ctx) return GA_ERR_ARG;
-  if (depth == 0) depth = 8;
-  bool known = false;
-  for (int d : ga::kSlDepths) known = known || d == depth;
-  if (!known) {
-    set_err(ctx, "ga_op_set_sl_depth: brick depth %d is not one of 4, 8, 12", depth);
-    return GA_ERR_ARG;
+  int d[2] = {state_depth == 0 ? 8 : state_depth, adjoint_depth == 0 ? 8 : adjoint_depth};
+  for (int i = 0; i < 2; ++i) {
+    bool known = false;
+    for (int k : ga::kSlDepths) known = known || k == d[i];
+    if (!known) {
+      set_err(ctx, "ga_op_set_sl_depth: brick depth %d is not one of 4, 8, 12", d[i]);
+      return GA_ERR_ARG;
+    }
   }
-  if (ctx->ef) ctx->ef->g.sl_bz = depth;
-  else ctx->ed->g.sl_bz = depth;
+  ga::Grid& g = ctx->ef ? ctx->ef->g : ctx->ed->g;
+  g.sl_bz = d[0];
+  g.sl_bz_adj = d[1];
   return GA_OK;
 }
 

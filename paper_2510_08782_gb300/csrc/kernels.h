@@ -12,7 +12,7 @@ constexpr int kThreads = 256;       // threads per CTA of the streaming kernels
 constexpr int kRedBlocks = 152 * 4; // CTAs of the reduction kernels (4 per SM of a GB300)
 constexpr int kMaxDots = 64;        // vectors per multi-dot call
 constexpr int kMaxWin = 63;         // window entries in the least-squares kernel
-constexpr int kSlDepths[3] = {8, 4, 12};  // brick depths of the FP32 3D transport steps (Grid::sl_bz)
+constexpr int kSlDepths[3] = {8, 4, 12};  // brick depths of the FP32 3D transport steps (Grid::sl_bz, sl_bz_adj)
 constexpr int kRegFftLen = 256;      // axis length of the register-resident derivative passes
 constexpr int kRegFftPencils = 16;   // complex pencils per CTA of those passes
 

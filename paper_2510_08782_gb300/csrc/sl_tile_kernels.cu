@@ -683,11 +683,12 @@ cudaError_t launch_mode_zb(const Grid& g, const float* f, const float* mu, const
   return cudaGetLastError();
 }
 
-// Brick depths the setup autotuner chooses from (Grid::sl_bz); every depth gives the same values.
+// Brick depths the setup autotuner chooses from (Grid::sl_bz for the state steps, sl_bz_adj for the
+// adjoint steps); every depth gives the same values.
 template <int MODE>
 cudaError_t launch_mode(const Grid& g, const float* f, const float* mu, const float* disp, float* out, float ht,
                         const float2* qin, float2* qout, cudaStream_t st) {
-  switch (g.sl_bz) {
+  switch (MODE >= 2 ? g.sl_bz_adj : g.sl_bz) {
     case 4: return launch_mode_zb<MODE, 4>(g, f, mu, disp, out, ht, qin, qout, st);
     case 12: return launch_mode_zb<MODE, 12>(g, f, mu, disp, out, ht, qin, qout, st);
     default: return launch_mode_zb<MODE, 8>(g, f, mu, disp, out, ht, qin, qout, st);

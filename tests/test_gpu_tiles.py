@@ -90,13 +90,14 @@ def test_set_tiles_rejects_bad_shapes():
 @pytest.mark.parametrize("model", ["continuity", "advection"])
 @pytest.mark.parametrize("shape", [(40, 48, 64), (30, 16, 40)])
 def test_every_brick_depth_gives_identical_transport(shape, model):
-    """The brick depth of the FP32 3D transport steps (z voxels per thread) is chosen at setup by timing;
-    every depth gives bit-identical states, adjoint states and gradients, including a ragged last brick
-    along z (30 is no multiple of 4, 8 or 12)."""
+    """The brick depths of the FP32 3D state and adjoint steps (z voxels per thread) are chosen at setup by
+    timing; every combination gives bit-identical states, adjoint states and gradients, including a
+    ragged last brick along z (30 is no multiple of 4, 8 or 12)."""
     from paper_2510_08782_gb300 import GaError, ga_op_adjoint, ga_op_forward, ga_op_get_sl_depth, ga_op_set_sl_depth
 
     P, v, m0 = _problem(shape, "mixed", model=model)
-    assert ga_op_get_sl_depth(P.ctx) in (4, 8, 12)
+    sd, ad = ga_op_get_sl_depth(P.ctx)
+    assert sd in (4, 8, 12) and ad in (4, 8, 12)
     vd = to_dev(v, "mixed")
     lam1 = to_dev(np.random.default_rng(2).standard_normal(shape), "mixed")
 
@@ -110,13 +111,16 @@ def test_every_brick_depth_gives_identical_transport(shape, model):
         return [host(st), host(la), host(g), np.array([obj])]
 
     outs = {}
-    for depth in (4, 8, 12):
-        ga_op_set_sl_depth(P.ctx, depth)
-        assert ga_op_get_sl_depth(P.ctx) == depth
-        outs[depth] = run()
-    for depth in (4, 12):
-        for x, y in zip(outs[depth], outs[8]):
-            assert np.array_equal(x, y)
-    with pytest.raises(GaError) as e:
-        ga_op_set_sl_depth(P.ctx, 5)
-    assert e.value.status == 1
+    for depths in ((4, 4), (8, 8), (12, 12), (12, 4), (4, 12)):  # (state steps, adjoint steps)
+        ga_op_set_sl_depth(P.ctx, *depths)
+        assert ga_op_get_sl_depth(P.ctx) == depths
+        outs[depths] = run()
+    for depths, out in outs.items():
+        for x, y in zip(out, outs[(8, 8)]):
+            assert np.array_equal(x, y), depths
+    for bad in ((5, 8), (8, 16)):
+        with pytest.raises(GaError) as e:
+            ga_op_set_sl_depth(P.ctx, *bad)
+        assert e.value.status == 1
+    ga_op_set_sl_depth(P.ctx, 0, 0)
+    assert ga_op_get_sl_depth(P.ctx) == (8, 8)
