@@ -101,6 +101,9 @@ template <typename T> struct Engine : EngineBase {
   cx<T>* qp[2] = {nullptr, nullptr};            // (pi, pi mu) pairs of the continuity state chain
   const T* q_src = nullptr;
   int q_idx = 0;
+  cx<T>* ap[2] = {nullptr, nullptr};            // (lambda, lambda mu) pairs of the advection adjoint chain
+  const T* a_src = nullptr;
+  int a_idx = 0;
   std::vector<void*> allocs;
   void* pinned = nullptr;
   double* hres = nullptr;
@@ -252,6 +255,10 @@ template <typename T> struct Engine : EngineBase {
       al(qp[0], nv);
       al(qp[1], nv);
     }
+    if (std::is_same<T, float>::value && dim == 3 && model != GA_MODEL_CONTINUITY) {
+      al(ap[0], nv);
+      al(ap[1], nv);
+    }
   }
 
   void init(ga_ctx* c, const void* hm0, const void* hm1, int mem) {
@@ -391,6 +398,7 @@ template <typename T> struct Engine : EngineBase {
           best_f = mf;
         }
         g.sl_bz_adj = zb;
+        adjoint_chain_reset();
         const float ma = timed([&] {
           sl_adjoint(m1, tmp[1]);
           sl_adjoint(m0, tmp[1]);
@@ -465,9 +473,26 @@ template <typename T> struct Engine : EngineBase {
     ck(launch_sl_forward<T>(g, model == GA_MODEL_CONTINUITY, src, xm, mu, dst, (T)ht, st, qin, qout), "sl_forward");
     prof_end(PROF_SL_FWD);
   }
+  // One adjoint step. Advection adjoint steps (two fields, lambda and lambda mu) of FP32 3D grids chain
+  // their pairs the same way through ap, with their own chain state (a backward sweep interleaves
+  // recomputed state steps).
+  void adjoint_chain_reset() {
+    a_src = nullptr;
+    a_idx = 0;
+  }
   void sl_adjoint(const T* src, T* dst) {
+    cx<T>* qin = nullptr;
+    cx<T>* qout = nullptr;
+    if (ap[0]) {
+      if (src != nullptr && src == a_src) {
+        qin = ap[a_idx];
+        a_idx ^= 1;
+      }
+      qout = ap[a_idx];
+      a_src = dst;
+    }
     prof_begin(PROF_SL_ADJ);
-    ck(launch_sl_adjoint<T>(g, model == GA_MODEL_CONTINUITY, src, xp, mu, dst, (T)ht, st), "sl_adjoint");
+    ck(launch_sl_adjoint<T>(g, model == GA_MODEL_CONTINUITY, src, xp, mu, dst, (T)ht, st, qin, qout), "sl_adjoint");
     prof_end(PROF_SL_ADJ);
   }
   void deriv(int axis, const T* f, const T* mult, T* out, double coef, bool acc) {
@@ -702,6 +727,7 @@ template <typename T> struct Engine : EngineBase {
   // buffer; a captured launch sequence therefore never depends on host state left by other calls).
   void body_force(const T* lam_init) {
     seg_base = last_segment();
+    adjoint_chain_reset();
     ck(cudaMemsetAsync(body, 0, sizeof(T) * vl, st), "memset body");
     const T* lcur = lam_init;
     int pp = (lam_init == lam[0]) ? 1 : 0;
@@ -1888,6 +1914,7 @@ ga_status ga_op_adjoint(ga_ctx* ctx, const void* v, const void* lam1, void* lams
     e.ck(launch_departure<T>(e.g, vv, e.xm, e.xp, (T)e.ht, e.st), "departure");
     const long long nv = e.nv;
     e.ck(cudaMemcpyAsync(out + (long long)e.nt * nv, lam1, sizeof(T) * nv, cudaMemcpyDeviceToDevice, e.st), "copy");
+    e.adjoint_chain_reset();
     for (int j = e.nt - 1; j >= 0; --j) e.sl_adjoint(out + (long long)(j + 1) * nv, out + (long long)j * nv);
     e.ck(cudaStreamSynchronize(e.st), "sync");
   });

@@ -90,7 +90,7 @@ cudaError_t launch_sl_tile(const Grid& g, int adjoint, int continuity, const flo
 // One adjoint step lambda_j from lambda_{j+1} (advection: with the source lambda div v).
 template <typename T>
 cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const T* xp, const T* mu,
-                              T* out, T ht, cudaStream_t st);
+                              T* out, T ht, cudaStream_t st, const cx<T>* qin = nullptr, cx<T>* qout = nullptr);
 
 // ---- reductions and vector kernels (reduce_kernels.cu) ---------------------------------------
 // out[i] = sum_j a[j] b_i[j] for i < count (count <= 32), FP64 compensated; out is device memory.

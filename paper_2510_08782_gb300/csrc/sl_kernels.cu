@@ -231,9 +231,9 @@ cudaError_t launch_sl_forward(const Grid& g, int continuity, const T* m, const T
 
 template <typename T>
 cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const T* xp, const T* mu, T* out,
-                              T ht, cudaStream_t st) {
+                              T ht, cudaStream_t st, const cx<T>* qin, cx<T>* qout) {
   if constexpr (std::is_same<T, float>::value) {
-    if (g.dim == 3) return launch_sl_tile(g, 1, continuity, lam, xp, mu, out, ht, st);
+    if (g.dim == 3) return launch_sl_tile(g, 1, continuity, lam, xp, mu, out, ht, st, qin, qout);
   }
   const unsigned gr = grid_for(g.nvox);
   if (g.dim == 3) {
@@ -263,7 +263,7 @@ cudaError_t launch_sl_adjoint(const Grid& g, int continuity, const T* lam, const
   template cudaError_t launch_sl_forward<T>(const Grid&, int, const T*, const T*, const T*, T*, T,    \
                                             cudaStream_t, const cx<T>*, cx<T>*);                                           \
   template cudaError_t launch_sl_adjoint<T>(const Grid&, int, const T*, const T*, const T*, T*, T,    \
-                                            cudaStream_t);
+                                            cudaStream_t, const cx<T>*, cx<T>*);
 GA_INST(float)
 GA_INST(double)
 #undef GA_INST
