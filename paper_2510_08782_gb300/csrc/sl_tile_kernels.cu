@@ -1,11 +1,12 @@
 // Tiled FP32 semi-Lagrangian step for 3D grids (Sec. 2.2; same arithmetic as sl_kernels.cu).
 //
-// A CTA owns a brick of 32 x 8 x ZB voxels (x contiguous; brick depth ZB = 4, 8 or 12). It stages the
-// brick plus a periodic halo (4 cells below / 4 above in x, 3 / 3 in y and z) of the transported
-// field into shared memory with 16-byte copies (and mu for the two-field steps). Each thread owns a
-// column of ZB voxels along z: a departure point whose integer offset lies in [-2, 1] on every axis
-// reads its 64 taps from shared memory; any other departure point reads the field from global
-// memory, so every displacement is handled exactly.
+// A CTA owns a brick of 32 x 8 x 8 voxels (x contiguous). It stages the brick plus a periodic halo
+// (4 cells below / 4 above in x, 3 / 3 in y and z) of the transported field into shared memory with
+// 16-byte cp.async copies (and mu for the two-field steps). Each thread owns a column of 8 voxels
+// along z and interpolates them one by one: a departure point whose integer offset lies in [-2, 1]
+// on every axis reads its 64 taps from shared memory (the product f * mu is formed tap by tap); any
+// other departure point reads the field from global memory, so every displacement is handled
+// exactly.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -190,63 +191,6 @@ __device__ __forceinline__ void stage_pairs_async(float2* dst, const float2* __r
   }
 }
 
-// Stage one brick's tile of `src` as x-pairs (f[x], f[x + 1]) into the pair layout (row pitch TXP) at `dst`
-// (all threads of the CTA): one-field steps then read a stencil row of four taps as two 64-bit loads.
-// The pair at the last tile column (x + 1 outside the tile) is never read. The 16-byte chunks go
-// through registers, three tile rows per warp at a time: lane l < 30 takes chunk l % 10 of row l / 10
-// (a fixed x offset per lane), gets the next chunk's first element from lane l + 1, and stores its four
-// pairs as two 16-byte shared stores.
-template <int ZB>
-__device__ __forceinline__ void stage_xpairs(float2* dst, const float* __restrict__ src, const BrickIdx& bi, int n0,
-                                             int n1, int n2, bool vec) {
-  constexpr int TZ = Tile<ZB>::TZ;
-  const int gx0 = bi.bx * BX - XOFF, gy0 = bi.by * BY - H - 1, gz0 = bi.bz * ZB - H - 1;
-  if (vec) {  // n2 % 4 == 0, n2 >= TXA, n1 >= TY, n0 >= TZ (see stage_async)
-    constexpr int CX = TXA / 4, ROWS = TY * TZ, WARPS = kTileThreads / 32;
-    constexpr int IT = (ROWS + 3 * WARPS - 1) / (3 * WARPS);
-    static_assert(3 * CX <= 32, "three tile rows of chunks per warp");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sub = lane / CX, cx = lane % CX;  // lanes 30 and 31: sub == 3, no chunk
-    int gx = gx0 + 4 * cx;
-    gx = gx < 0 ? gx + n2 : (gx >= n2 ? gx - n2 : gx);
-    float4 q[IT];
-#pragma unroll
-    for (int i = 0; i < IT; ++i) {
-      const int row = 3 * (warp + WARPS * i) + sub;
-      q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (sub < 3 && row < ROWS) {
-        const int ty = row % TY, tz = row / TY;
-        int gy = gy0 + ty, gz = gz0 + tz;
-        gy = gy < 0 ? gy + n1 : (gy >= n1 ? gy - n1 : gy);
-        gz = gz < 0 ? gz + n0 : (gz >= n0 ? gz - n0 : gz);
-        q[i] = __ldg(reinterpret_cast<const float4*>(src + ((size_t)gz * n1 + gy) * n2 + gx));
-      }
-    }
-    // Each lane's 16-byte store covers banks 8 (cx % 4) + 4 h .. + 3 for the half h it stores first; this
-    // h spreads the 30 lanes' first stores over all 32 banks (at most 5 lanes per group of 4 banks).
-    const int h = ((cx >> 2) ^ sub) & 1;
-#pragma unroll
-    for (int i = 0; i < IT; ++i) {
-      const float nx = __shfl_down_sync(0xffffffffu, q[i].x, 1);  // the row's next chunk (unused at its end)
-      const int row = 3 * (warp + WARPS * i) + sub;
-      if (sub < 3 && row < ROWS) {
-        float4* d = reinterpret_cast<float4*>(dst + row * TXP + 4 * cx);
-        const float4 lo = make_float4(q[i].x, q[i].y, q[i].y, q[i].z), hi = make_float4(q[i].z, q[i].w, q[i].w, nx);
-        d[h] = h ? hi : lo;
-        d[h ^ 1] = h ? lo : hi;
-      }
-    }
-  } else {
-    for (int e = threadIdx.x; e < TXA * TY * TZ; e += blockDim.x) {
-      const int tx = e % TXA, row = e / TXA;
-      const int ty = row % TY, tz = row / TY;
-      const int gy = wrap_any(gy0 + ty, n1), gz = wrap_any(gz0 + tz, n0);
-      const float* r = src + ((size_t)gz * n1 + gy) * n2;
-      dst[row * TXP + tx] = make_float2(__ldg(r + wrap_any(gx0 + tx, n2)), __ldg(r + wrap_any(gx0 + tx + 1, n2)));
-    }
-  }
-}
-
 // ---- scalar / packed-pair arithmetic with explicit rounding ----
 // The pair type float2 runs two independent lanes through the FP32x2 FMA path of sm_100+; the scalar
 // overloads perform the same operations in the same order, so a voxel's interpolant does not depend
@@ -295,41 +239,12 @@ __device__ __forceinline__ V interp64(const V* wz, const V* wy, const V* wx, Loa
   return acc;
 }
 
-// One field from the x-pair tile (f[x], f[x + 1]) of pitch TXP, one voxel: base is the pair index of the
-// stencil's first tap, t* the offsets in [0, 1). A stencil row is two pairs, taps (0, 1) and (2, 3);
-// the packed lanes carry the sums over the even and the odd x taps through the x, y and z sums, and
-// their sum is the interpolant. Every voxel takes this one sequence, alone or beside another.
-__device__ __forceinline__ float interp64_xpairs(const float2* sp, int base, float tz, float ty, float tx) {
-  float2 wz[4], wy[4];
-  lagrange4v(vsplat<float2>(tz), wz);
-  lagrange4v(vsplat<float2>(ty), wy);
-  // x weights as the pairs (w0, w1), (w2, w3), each element formed as in lagrange4v
-  const float tp1 = __fadd_rn(tx, 1.f), tm1 = __fadd_rn(tx, -1.f), tm2 = __fadd_rn(tx, -2.f);
-  const float a = __fmul_rn(tx, tm1), b = __fmul_rn(tp1, tm2);
-  const float2 w01 = vmul(vmul(make_float2(a, b), make_float2(tm2, tm1)), make_float2(-1.f / 6.f, 0.5f));
-  const float2 w23 = vmul(vmul(make_float2(b, a), make_float2(tx, tp1)), make_float2(-0.5f, 1.f / 6.f));
-  float2 acc;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    float2 ay;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int o = base + (c * TY + r) * TXP;
-      const float2 row = vfma(sp[o + 2], w23, vmul(sp[o], w01));
-      ay = r == 0 ? vmul(row, wy[0]) : vfma(row, wy[r], ay);
-    }
-    acc = c == 0 ? vmul(ay, wz[0]) : vfma(ay, wz[c], acc);
-  }
-  return __fadd_rn(acc.x, acc.y);
-}
-
 __device__ __forceinline__ bool in_halo(float fz, float fy, float fx) {
   return fz >= -H && fz <= H - 1 && fy >= -H && fy <= H - 1 && fx >= -H && fx <= H - 1;
 }
 
 // One voxel (brick-local z index v, global index idx): shared-memory taps when the stencil lies in the
-// halo, global taps otherwise. `sf` is the pair tile: (f, f mu) for the two-field steps, the x-pairs
-// (f[x], f[x + 1]) for the one-field steps.
+// halo, global taps otherwise. Two-field steps read the interleaved (f, f mu) tile `sf`.
 template <int MODE>
 __device__ __forceinline__ void sl_single(const float* __restrict__ f, const float* __restrict__ mu,
                                           float* __restrict__ out, float2* __restrict__ qout, const float* sf, int col,
@@ -339,16 +254,17 @@ __device__ __forceinline__ void sl_single(const float* __restrict__ f, const flo
   const float fz = floorf(vz), fy = floorf(vy), fx = floorf(vx);
   float P = 0.f, S = 0.f;
   if (in_halo(fz, fy, fx)) {
-    const int base = col + ((v + H + (int)fz) * TY + (int)fy) * TXP + (int)fx;  // pair-layout index
-    if (NF == 2) {
-      float wz[4], wy[4], wx[4];
-      lagrange4v(vz - fz, wz);
-      lagrange4v(vy - fy, wy);
-      lagrange4v(vx - fx, wx);
+    float wz[4], wy[4], wx[4];
+    lagrange4v(vz - fz, wz);
+    lagrange4v(vy - fy, wy);
+    lagrange4v(vx - fx, wx);
+    if (NF == 2) {  // col is the pair-layout index here
+      const int base = col + ((v + H + (int)fz) * TY + (int)fy) * TXP + (int)fx;
       P = interp64<TXP, float>(wz, wy, wx, [&](int o) { return sf[2 * (base + o)]; });
       S = interp64<TXP, float>(wz, wy, wx, [&](int o) { return sf[2 * (base + o) + 1]; });
     } else {
-      P = interp64_xpairs(reinterpret_cast<const float2*>(sf), base, vz - fz, vy - fy, vx - fx);
+      const int base = col + ((v + H + (int)fz) * TY + (int)fy) * TXA + (int)fx;
+      P = interp64<TXA, float>(wz, wy, wx, [&](int o) { return sf[base + o]; });
     }
   } else {
     gather_global<NF>(f, mu, gz, gy, gx, vz, vy, vx, n0, n1, n2, P, S);
@@ -360,13 +276,12 @@ __device__ __forceinline__ void sl_single(const float* __restrict__ f, const flo
 // MODE 1: continuity state step         out = P - ht/2 (S + mu (P - ht S)),  P = I[f], S = I[f mu]
 // MODE 2: advection adjoint step        out = L + ht/2 (S + mu (L + ht S)),  L = I[f], S = I[f mu]
 // MODE 3: continuity adjoint step       out = I[f](X+)
-// One CTA per brick, whose tile of 8-byte pairs lies in shared memory; several CTAs per SM overlap one
-// brick's copies with another's interpolation. The two-field steps copy f and mu asynchronously and
-// interleave them into (f, f mu) pairs, so the product is formed once per tile element (or copy the
-// pairs the previous step wrote); the one-field steps load f as x-pairs (f[x], f[x + 1]), so a stencil
-// row of four taps is two 64-bit loads. Each thread walks its column of voxels two at a time, with the
-// taps read from shared memory at compile-time offsets from one base index per voxel: the two fields of
-// a voxel run as one packed FP32x2 pair, and so do the even and odd x taps of a one-field voxel.
+// One CTA per brick. The tile (and, for the two-field steps, mu) is copied asynchronously into
+// shared memory; several CTAs per SM overlap one brick's copies with another's interpolation. For
+// the two-field steps the staged mu tile is then overwritten with f * mu, so the product is formed
+// once per tile element. Each thread walks its column of 8 voxels two at a time: the pair's weights
+// and its 64-tap sums (per field) run as packed FP32x2 operations, with the taps read from shared
+// memory at compile-time offsets from one base index per voxel.
 template <int MODE, int ZB>
 __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const float* __restrict__ mu,
                                              const float* __restrict__ disp, float* __restrict__ out, int n0, int n1,
@@ -382,6 +297,13 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
   const int nbx = (n2 + BX - 1) / BX, nby = (n1 + BY - 1) / BY;
   const BrickIdx bi = brick_of(blockIdx.x, nbx, nby);
   const bool pairs_in = NF == 2 && qin != nullptr;  // the previous step wrote (f, f mu): stage them as they are
+  if (pairs_in) {
+    stage_pairs_async<ZB>(reinterpret_cast<float2*>(smem), qin, bi, n0, n1, n2, vec != 0);
+  } else {
+    stage_async<ZB>(smem, f, bi, n0, n1, n2, vec != 0);
+    if (NF == 2) stage_async<ZB>(smem + TILEA, mu, bi, n0, n1, n2, vec != 0);
+  }
+  cp_async_commit();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gx = bi.bx * BX + lane, gy = bi.by * BY + warp;
   const bool active = gx < n2 && gy < n1;
@@ -398,16 +320,7 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
     xa = disp[2 * nv + ia], xb = disp[2 * nv + ib];
     if (NF == 2) ma = mu[ia], mb = mu[ib];
   };
-  if (NF == 1) {
-    if (active && nz >= 2) fetch(0);  // in flight while the tile is loaded
-    stage_xpairs<ZB>(reinterpret_cast<float2*>(smem), f, bi, n0, n1, n2, vec != 0);
-  } else if (pairs_in) {
-    stage_pairs_async<ZB>(reinterpret_cast<float2*>(smem), qin, bi, n0, n1, n2, vec != 0);
-  } else {
-    stage_async<ZB>(smem, f, bi, n0, n1, n2, vec != 0);
-    stage_async<ZB>(smem + TILEA, mu, bi, n0, n1, n2, vec != 0);
-  }
-  cp_async_commit();
+  if (NF == 1 && active && nz >= 2) fetch(0);
   if (NF == 2 && active && nz >= 2) {
     // the first pair's loads follow the tile conversion (which needs the registers): pull their lines
     // into L2 now, while the tile copies are in flight
@@ -447,8 +360,8 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
     __syncthreads();
   }
   if (!active) return;
-  // pair-tile index of (z = 0, y, x) minus the x tap offset
-  const int col = (warp + H) * TXP + lane + XOFF - 1;
+  // tile index of (z = 0, y, x) minus the x tap offset (in the pair layout for two-field steps)
+  const int col = (warp + H) * (NF == 2 ? TXP : TXA) + lane + XOFF - 1;
 
   int v = 0;
 #pragma unroll 1
@@ -459,8 +372,9 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
     const float fza = floorf(cza), fya = floorf(cya), fxa = floorf(cxa);
     const float fzb = floorf(czb), fyb = floorf(cyb), fxb = floorf(cxb);
     if (in_halo(fza, fya, fxa) && in_halo(fzb, fyb, fxb)) {
-      const int ba = col + ((v + H + (int)fza) * TY + (int)fya) * TXP + (int)fxa;
-      const int bb = col + ((v + 1 + H + (int)fzb) * TY + (int)fyb) * TXP + (int)fxb;
+      constexpr int PT = NF == 2 ? TXP : TXA;
+      const int ba = col + ((v + H + (int)fza) * TY + (int)fya) * PT + (int)fxa;
+      const int bb = col + ((v + 1 + H + (int)fzb) * TY + (int)fyb) * PT + (int)fxb;
       float2 wz[4], wy[4], wx[4];
       if (NF == 2) {
         // per voxel, the two fields as one packed pair; the weights carry the voxel's value in both
@@ -479,9 +393,13 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
         const float yb = step_value<MODE>(B.x, B.y, cmb, ht);
         out[ib] = yb;
         if (qout) qout[ib] = make_float2(yb, yb * cmb);
-      } else {  // one field: each voxel's even and odd x taps as one packed pair
-        out[ia] = step_value<MODE>(interp64_xpairs(sp, ba, cza - fza, cya - fya, cxa - fxa), 0.f, cma, ht);
-        out[ib] = step_value<MODE>(interp64_xpairs(sp, bb, czb - fzb, cyb - fyb, cxb - fxb), 0.f, cmb, ht);
+      } else {  // one field: the pair of voxels as one packed pair
+        lagrange4v(make_float2(cza - fza, czb - fzb), wz);
+        lagrange4v(make_float2(cya - fya, cyb - fyb), wy);
+        lagrange4v(make_float2(cxa - fxa, cxb - fxb), wx);
+        const float2 P = interp64<TXA, float2>(wz, wy, wx, [&](int o) { return make_float2(sf[ba + o], sf[bb + o]); });
+        out[ia] = step_value<MODE>(P.x, 0.f, cma, ht);
+        out[ib] = step_value<MODE>(P.y, 0.f, cmb, ht);
       }
     } else {
       sl_single<MODE>(f, mu, out, qout, sf, col, ia, bi.bz * ZB + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
@@ -598,8 +516,8 @@ __device__ __forceinline__ bool column_walk(int col, Disp&& disp, Tap&& tap, Emi
   return true;
 }
 
-// Both kinds of step hold a pair tile of 8-byte elements (row pitch TXP): 53.8 KB at brick depth 4,
-// 75.3 KB at depth 8, 96.8 KB at depth 12, so 4, 3 or 2 CTAs fit on an SM.
+// Two-field steps (MODE 1, 2) fit 3 CTAs per SM by shared memory; one-field steps (MODE 0, 3) fit 4
+// when held to 64 registers.
 template <int MODE, int ZB>
 __global__ void __launch_bounds__(256, ZB <= 8 ? 3 : 2) k_sl_tile2(const float* __restrict__ f,
                                                                   const float* __restrict__ mu,
@@ -610,7 +528,7 @@ __global__ void __launch_bounds__(256, ZB <= 8 ? 3 : 2) k_sl_tile2(const float* 
   sl_tile_body<MODE, ZB>(f, mu, disp, out, n0, n1, n2, ht, vec, qin, qout);
 }
 template <int MODE, int ZB>
-__global__ void __launch_bounds__(256, ZB <= 4 ? 4 : (ZB <= 8 ? 3 : 2)) k_sl_tile1(const float* __restrict__ f, const float* __restrict__ mu,
+__global__ void __launch_bounds__(256, 4) k_sl_tile1(const float* __restrict__ f, const float* __restrict__ mu,
                                                      const float* __restrict__ disp, float* __restrict__ out, int n0,
                                                      int n1, int n2, float ht, int vec, const float2* __restrict__ qin,
                                                      float2* __restrict__ qout) {
@@ -741,9 +659,8 @@ cudaError_t launch_mode_zb(const Grid& g, const float* f, const float* mu, const
                            const float2* qin, float2* qout, cudaStream_t st) {
   constexpr int NF = (MODE == 1 || MODE == 2) ? 2 : 1;
   constexpr int TILEA = Tile<ZB>::A, TILEP = Tile<ZB>::P;
-  // the pair tile; two-field steps stage the f and mu tiles into the same bytes first (TILEP >= TILEA)
-  static_assert(TILEP >= TILEA, "pair pitch below the staged row");
-  const size_t sm = sizeof(float2) * TILEP;
+  // two-field steps: the f and mu tiles, then the same bytes (plus row padding) as (f, f mu) pairs
+  const size_t sm = NF == 2 ? sizeof(float) * (2 * TILEP > 2 * TILEA ? 2 * TILEP : 2 * TILEA) : sizeof(float) * TILEA;
   void (*kern)(const float*, const float*, const float*, float*, int, int, int, float, int, const float2*, float2*);
   if constexpr (NF == 2) kern = k_sl_tile2<MODE, ZB>;
   else kern = k_sl_tile1<MODE, ZB>;
