@@ -1,6 +1,7 @@
 // Runtime behind the C ABI of include/ga.h and include/ga_ops.h.
 //
-// One context owns every device buffer of one problem and orders all work on one stream. The
+// One context owns every device buffer of one problem and orders its work on one stream (the body
+// force's derivative passes run on a second stream of the context, joined by events). The
 // gradient evaluation (Eq. (3)) runs as: the regulariser value 1/2 <v, w> with w = alpha L v (carried
 // by the solver with v; formed by the transform for a caller's v), mu = div v by 1D derivative
 // passes, RK2 departure points, n_t state steps (all states or checkpoints every K), mismatch and
@@ -109,10 +110,23 @@ template <typename T> struct Engine : EngineBase {
   double* hres = nullptr;
 
   T *m0 = nullptr, *m1 = nullptr, *xm = nullptr, *xp = nullptr, *mu = nullptr;
-  T *lam[2] = {nullptr, nullptr}, *body = nullptr, *tmp[2] = {nullptr, nullptr};
+  // adjoint states: a ring, so the adjoint steps run ahead of the body-force passes that read them
+  static constexpr int kLamRing = 6;
+  T* lam[kLamRing] = {};
+  T *body = nullptr, *tmp[2] = {nullptr, nullptr};
   T* wtmp = nullptr;  // alpha L v for calls that do not carry it
-  T *states = nullptr, *seg = nullptr, *io_a = nullptr, *io_b = nullptr;
-  int nslots = 0, seg_base = -1;
+  // recomputed checkpoint segments: two buffers, so a recompute does not wait for the passes that
+  // read the previous segment; seg_base[b] is the first state index of the segment buffer b holds
+  T *states = nullptr, *seg[2] = {nullptr, nullptr}, *io_a = nullptr, *io_b = nullptr;
+  int nslots = 0, seg_base[2] = {-1, -1}, seg_next = 0;
+  // The body force's derivative passes run on st2, overlapped with the adjoint steps and recomputed
+  // state steps on st. Group g (the passes of one trapezoid pair) ends with bf_ev[g] on st2; a buffer
+  // that group read is written again on st only after st has waited for bf_ev[g].
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t bf_fork = nullptr, bf_join = nullptr;
+  std::vector<cudaEvent_t> bf_ev;
+  int lam_reader[kLamRing] = {}, seg_reader[2] = {-1, -1}, bf_waited = -1;
+  bool bf_active = false;
   cx<T> *vh = nullptr, *bh = nullptr;
   double *dpart = nullptr, *dres = nullptr, *dM = nullptr, *dbeta = nullptr;
 
@@ -139,6 +153,10 @@ template <typename T> struct Engine : EngineBase {
     if (ev[0]) cudaEventDestroy(ev[0]);
     if (ev[1]) cudaEventDestroy(ev[1]);
     for (auto e : prof_ev) cudaEventDestroy(e);
+    for (auto e : bf_ev) cudaEventDestroy(e);
+    if (bf_fork) cudaEventDestroy(bf_fork);
+    if (bf_join) cudaEventDestroy(bf_join);
+    if (st2) cudaStreamDestroy(st2);
     for (auto ge : gexec)
       if (ge) cudaGraphExecDestroy(ge);
     if (gst) cudaStreamDestroy(gst);
@@ -212,15 +230,17 @@ template <typename T> struct Engine : EngineBase {
     al(xm, vl);
     al(xp, vl);
     al(mu, nv);
-    al(lam[0], nv);
-    al(lam[1], nv);
+    for (int i = 0; i < kLamRing; ++i) al(lam[i], nv);
     al(tmp[0], nv);
     al(tmp[1], nv);
     al(body, vl);
     al(io_a, vl);
     al(io_b, vl);
     al(states, (long long)nslots * nv);
-    if (K > 1) al(seg, (long long)(K - 1) * nv);
+    if (K > 1) {
+      al(seg[0], (long long)(K - 1) * nv);
+      al(seg[1], (long long)(K - 1) * nv);
+    }
     al(vh, g.nhalf * dim);
     al(bh, g.nhalf * dim);
     al(dpart, (long long)kMaxDots * kRedBlocks);
@@ -267,6 +287,11 @@ template <typename T> struct Engine : EngineBase {
     derive(c->desc, c->opts);
     ck(cudaEventCreate(&ev[0]), "cudaEventCreate");
     ck(cudaEventCreate(&ev[1]), "cudaEventCreate");
+    ck(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking), "body-force stream");
+    ck(cudaEventCreateWithFlags(&bf_fork, cudaEventDisableTiming), "cudaEventCreate");
+    ck(cudaEventCreateWithFlags(&bf_join, cudaEventDisableTiming), "cudaEventCreate");
+    bf_ev.resize(nt / 2 + 2);
+    for (auto& e : bf_ev) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
     layout([&](auto*& p, long long count) {
       using U = std::remove_reference_t<decltype(*p)>;
       p = dalloc<U>(count);
@@ -419,14 +444,16 @@ template <typename T> struct Engine : EngineBase {
 
   // ---- profiling hooks ------------------------------------------------------------------------
   enum { PROF_SL_FWD = 0, PROF_DERIV = 1, PROF_FFT = 2, PROF_SL_ADJ = 3, PROF_DERIV_PAIR = 4 };
-  void prof_begin(int cls) {
+  void prof_begin(int cls) { prof_begin(cls, st); }
+  void prof_end(int cls) { prof_end(cls, st); }
+  void prof_begin(int cls, cudaStream_t s) {
     if (prof_class != cls) return;
     if (prof_used + 2 > (int)prof_ev.size()) prof_flush();
-    ck(cudaEventRecord(prof_ev[prof_used], st), "cudaEventRecord");
+    ck(cudaEventRecord(prof_ev[prof_used], s), "cudaEventRecord");
   }
-  void prof_end(int cls) {
+  void prof_end(int cls, cudaStream_t s) {
     if (prof_class != cls) return;
-    ck(cudaEventRecord(prof_ev[prof_used + 1], st), "cudaEventRecord");
+    ck(cudaEventRecord(prof_ev[prof_used + 1], s), "cudaEventRecord");
     prof_used += 2;
     ++prof_launches;
   }
@@ -495,17 +522,18 @@ template <typename T> struct Engine : EngineBase {
     ck(launch_sl_adjoint<T>(g, model == GA_MODEL_CONTINUITY, src, xp, mu, dst, (T)ht, st, qin, qout), "sl_adjoint");
     prof_end(PROF_SL_ADJ);
   }
-  void deriv(int axis, const T* f, const T* mult, T* out, double coef, bool acc) {
-    prof_begin(PROF_DERIV);
-    ck(launch_deriv<T>(g, ft, axis, f, mult, out, (T)coef, acc, st), "deriv");
-    prof_end(PROF_DERIV);
+  void deriv(int axis, const T* f, const T* mult, T* out, double coef, bool acc) { deriv(axis, f, mult, out, coef, acc, st); }
+  void deriv(int axis, const T* f, const T* mult, T* out, double coef, bool acc, cudaStream_t s) {
+    prof_begin(PROF_DERIV, s);
+    ck(launch_deriv<T>(g, ft, axis, f, mult, out, (T)coef, acc, s), "deriv");
+    prof_end(PROF_DERIV, s);
   }
-  // out += coef mult d f + coef2 mult2 d f2 along `axis` (two time steps of the body force)
+  // out += coef mult d f + coef2 mult2 d f2 along `axis` (two time steps of the body force), on stream s
   void deriv_pair(int axis, const T* f, const T* mult, double coef, const T* f2, const T* mult2, double coef2,
-                  T* out) {
-    prof_begin(PROF_DERIV_PAIR);
-    ck(launch_deriv_pair<T>(g, ft, axis, f, mult, (T)coef, f2, mult2, (T)coef2, out, true, st), "deriv pair");
-    prof_end(PROF_DERIV_PAIR);
+                  T* out, cudaStream_t s) {
+    prof_begin(PROF_DERIV_PAIR, s);
+    ck(launch_deriv_pair<T>(g, ft, axis, f, mult, (T)coef, f2, mult2, (T)coef2, out, true, s), "deriv pair");
+    prof_end(PROF_DERIV_PAIR, s);
   }
   void r2c(const T* f, cx<T>* fh) {
     prof_begin(PROF_FFT);
@@ -586,29 +614,48 @@ template <typename T> struct Engine : EngineBase {
     for (int j = 0; j < nt; ++j) {
       T* dst;
       if (stored(j + 1)) dst = const_cast<T*>(slot(j + 1));
-      else if (jl >= 0 && j + 1 > jl) dst = seg + (long long)(j - jl) * nv;
+      else if (jl >= 0 && j + 1 > jl) dst = seg[0] + (long long)(j - jl) * nv;
       else dst = tmp[(j + 1) & 1];
       sl_forward(cur, dst);
       cur = dst;
     }
-    seg_base = jl;
+    segs_after_forward();
+  }
+  // The segment buffers as forward_all leaves them: the last segment (if any) in seg[0].
+  void segs_after_forward() {
+    seg_base[0] = last_segment();
+    seg_base[1] = -1;
+    seg_next = 1;
   }
 
+  // State j: a stored state, or one of a recomputed segment. A segment is recomputed from its
+  // checkpoint into the segment buffer used less recently, once the body-force passes that read that
+  // buffer's segment are done.
   const T* state(int j) {
     if (stored(j)) return slot(j);
     const int js = (j / K) * K;
-    if (seg_base != js) {
-      chain_reset();
-      const T* cur = slot(js);
-      const int last = (js + K - 1 < nt - 1) ? js + K - 1 : nt - 1;
-      for (int i = js + 1; i <= last; ++i) {
-        T* dst = seg + (long long)(i - js - 1) * nv;
-        sl_forward(cur, dst);
-        cur = dst;
-      }
-      seg_base = js;
+    for (int b = 0; b < 2; ++b)
+      if (seg_base[b] == js) return seg[b] + (long long)(j - js - 1) * nv;
+    const int b = seg_next;
+    seg_next ^= 1;
+    bf_wait(seg_reader[b]);
+    seg_reader[b] = -1;
+    chain_reset();
+    const T* cur = slot(js);
+    const int last = (js + K - 1 < nt - 1) ? js + K - 1 : nt - 1;
+    for (int i = js + 1; i <= last; ++i) {
+      T* dst = seg[b] + (long long)(i - js - 1) * nv;
+      sl_forward(cur, dst);
+      cur = dst;
     }
-    return seg + (long long)(j - js - 1) * nv;
+    seg_base[b] = js;
+    return seg[b] + (long long)(j - js - 1) * nv;
+  }
+  // st waits until body-force group grp (and every earlier one) is done on st2.
+  void bf_wait(int grp) {
+    if (grp <= bf_waited) return;
+    ck(cudaStreamWaitEvent(st, bf_ev[grp], 0), "wait body-force passes");
+    bf_waited = grp;
   }
 
   void issue_results(int count) {
@@ -723,34 +770,77 @@ template <typename T> struct Engine : EngineBase {
   // The trapezoid rule over t_j = j h_t, j = n_t .. 0, visits the time steps in pairs (j, j - 1): the
   // adjoint step to lambda_{j-1} is taken first, then one derivative pass per axis adds both steps'
   // terms (the two fields share each complex FFT). With n_t even, j = 0 is a single pass.
-  // Precondition: the last forward_all ran on the same velocity (its last segment is in the segment
-  // buffer; a captured launch sequence therefore never depends on host state left by other calls).
+  // The derivative passes of a pair (a group) run on st2 once st has produced their operands, so they
+  // overlap the next adjoint steps and segment recomputes on st; they still run one after another in
+  // the same order, so b is summed exactly as on one stream. The adjoint states rotate through
+  // kLamRing buffers and the recomputed segments through two: st overwrites a buffer only after the
+  // group that read it is done. st waits for st2 at the end.
+  // Precondition: the last forward_all ran on the same velocity (its last segment is in seg[0]; a
+  // captured launch sequence therefore never depends on host state left by other calls).
   void body_force(const T* lam_init) {
-    seg_base = last_segment();
+    segs_after_forward();
     adjoint_chain_reset();
     ck(cudaMemsetAsync(body, 0, sizeof(T) * vl, st), "memset body");
+    for (auto& r : lam_reader) r = -1;
+    seg_reader[0] = seg_reader[1] = -1;
+    bf_waited = -1;
+    auto ring_of = [&](const T* p) {
+      for (int i = 0; i < kLamRing; ++i)
+        if (p == lam[i]) return i;
+      return -1;
+    };
+    auto seg_of = [&](const T* p) {
+      for (int b = 0; b < 2; ++b)
+        if (seg[b] && p >= seg[b] && p < seg[b] + (long long)(K - 1) * nv) return b;
+      return -1;
+    };
+    int ring = (ring_of(lam_init) + 1) % kLamRing;  // the next ring buffer to write
+    auto next_lam = [&]() {
+      const int i = ring;
+      ring = (ring + 1) % kLamRing;
+      bf_wait(lam_reader[i]);
+      lam_reader[i] = -1;
+      return lam[i];
+    };
+    int grp = 0;
+    auto issue = [&](auto&& passes, const T* la, const T* lb, const T* ma, const T* mb) {
+      ck(cudaEventRecord(bf_fork, st), "fork");
+      ck(cudaStreamWaitEvent(st2, bf_fork, 0), "fork wait");
+      passes();
+      ck(cudaEventRecord(bf_ev[grp], st2), "group done");
+      for (const T* p : {la, lb}) {
+        const int i = p ? ring_of(p) : -1;
+        if (i >= 0) lam_reader[i] = grp;
+      }
+      for (const T* p : {ma, mb}) {
+        const int b = p ? seg_of(p) : -1;
+        if (b >= 0) seg_reader[b] = grp;
+      }
+      ++grp;
+    };
     const T* lcur = lam_init;
-    int pp = (lam_init == lam[0]) ? 1 : 0;
     const bool cont = model == GA_MODEL_CONTINUITY;
     auto coef_of = [&](int j) { return ht * ((j == 0 || j == nt) ? 0.5 : 1.0); };
     int j = nt;
     for (; j >= 1; j -= 2) {
       const T* mj = state(j);  // a stored state, or in the same segment as j - 1
-      T* lprev = lam[pp];
+      T* lprev = next_lam();
       sl_adjoint(lcur, lprev);  // lambda_{j-1}
-      pp ^= 1;
       const T* mj1 = state(j - 1);
       const double c0 = coef_of(j), c1 = coef_of(j - 1);
-      for (int c = 0; c < dim; ++c) {
-        if (cont)  // b -= h_t w_j pi_j grad lambda_j
-          deriv_pair(g.axis_of(c), lcur, mj, -c0, lprev, mj1, -c1, body + c * nv);
-        else  // b += h_t w_j lambda_j grad m_j
-          deriv_pair(g.axis_of(c), mj, lcur, c0, mj1, lprev, c1, body + c * nv);
-      }
+      issue(
+          [&] {
+            for (int c = 0; c < dim; ++c) {
+              if (cont)  // b -= h_t w_j pi_j grad lambda_j
+                deriv_pair(g.axis_of(c), lcur, mj, -c0, lprev, mj1, -c1, body + c * nv, st2);
+              else  // b += h_t w_j lambda_j grad m_j
+                deriv_pair(g.axis_of(c), mj, lcur, c0, mj1, lprev, c1, body + c * nv, st2);
+            }
+          },
+          lcur, lprev, mj, mj1);
       if (j - 1 >= 1) {
-        T* lnext = lam[pp];
+        T* lnext = next_lam();
         sl_adjoint(lprev, lnext);  // lambda_{j-2}
-        pp ^= 1;
         lcur = lnext;
       } else {
         lcur = lprev;
@@ -759,13 +849,22 @@ template <typename T> struct Engine : EngineBase {
     if (j == 0) {  // n_t even: the last time step alone
       const T* m0s = state(0);
       const double c0 = coef_of(0);
-      for (int c = 0; c < dim; ++c) {
-        if (cont)
-          deriv(g.axis_of(c), lcur, m0s, body + c * nv, -c0, true);
-        else
-          deriv(g.axis_of(c), m0s, lcur, body + c * nv, c0, true);
-      }
+      issue(
+          [&] {
+            for (int c = 0; c < dim; ++c) {
+              if (cont)
+                deriv(g.axis_of(c), lcur, m0s, body + c * nv, -c0, true, st2);
+              else
+                deriv(g.axis_of(c), m0s, lcur, body + c * nv, c0, true, st2);
+            }
+          },
+          lcur, nullptr, m0s, nullptr);
     }
+    ck(cudaEventRecord(bf_join, st2), "join");
+    ck(cudaStreamWaitEvent(st, bf_join, 0), "join wait");
+    for (auto& r : lam_reader) r = -1;
+    seg_reader[0] = seg_reader[1] = -1;
+    bf_waited = -1;
   }
 
   // Reduced gradient g = alpha L v + (P) b (Eq. (3)) into gout (vl). w = alpha L v: carried by the
@@ -889,7 +988,7 @@ template <typename T> struct Engine : EngineBase {
     ck(cudaMemsetAsync(G, 0, sizeof(T) * vl, st), "memset G");
     if (rT != lam[0]) ck(cudaMemcpyAsync(lam[0], rT, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st), "copy r");
     int pp = 0;
-    seg_base = last_segment();  // dto_forward ran just before on the same v
+    segs_after_forward();  // dto_forward ran just before on the same v
     for (int j = nt - 1; j >= 0; --j) {
       const T* mj = state(j);
       ck(launch_dto_accum<T>(g, lam[pp], mj, xm, G, (T)coef, st), "dto accumulate");

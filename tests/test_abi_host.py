@@ -172,9 +172,10 @@ def test_workspace_planner_follows_the_context_layout(libga):
     # one more window slot: one more iterate (v and alpha L v) and gradient, and a larger FP64 Gram
     w6 = wb(*_desc_opts(libga, n, window=6))
     assert w6 - base == 3 * vl * s + (7 * 7 - 6 * 6) * 8
-    # checkpoints every 4 of 16 steps: 4 stored states and 3 recompute slots instead of 16 states
+    # checkpoints every 4 of 16 steps: 4 stored states and two segment buffers of 3 recomputed states
+    # instead of 16 states
     ck = wb(*_desc_opts(libga, n, K=4))
-    assert base - ck == (16 - 4 - 3) * nv * s
+    assert base - ck == (16 - 4 - 2 * 3) * nv * s
     # FP64 doubles every field; the FP64 scratch arrays and the Gram do not change
     d64 = wb(*_desc_opts(libga, n, prec=0))
     fixed = base - (d64 - base)
