@@ -122,7 +122,10 @@ typedef struct ga_ctx ga_ctx; /* opaque; owns all device memory of one problem *
 
 /* Create a context on the current CUDA device. m0, m1: template/reference (or densities pi0,
  * pi1) as scalar fields of the descriptor's element type. stream: a cudaStream_t (NULL = the
- * legacy default stream) on which all work of this context is ordered. Before it allocates
+ * legacy default stream) on which all work of this context is ordered. (Inside a gradient the
+ * body force's derivative passes run on a second stream the context owns, forked from this stream
+ * by an event and joined back to it before the gradient's next step, so to the caller every call
+ * is still ordered on `stream`; in a captured graph the fork and join are graph edges.) Before it allocates
  * anything, ga_setup compares the workspace (ga_workspace_bytes) with the device's free memory and
  * returns GA_ERR_NOMEM, with the two figures in the message, when it does not fit; a cudaMalloc that
  * still fails later (another allocator took the memory meanwhile) also returns GA_ERR_NOMEM. Either
