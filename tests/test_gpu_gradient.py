@@ -136,6 +136,40 @@ def test_checkpointed_gradient_equals_stored(prec, nt, ckpt):
         assert np.array_equal(host(v0), host(vk)) and s0.obj == sk.obj
 
 
+@pytest.mark.parametrize("model,nt,ckpt", [("continuity", 16, 4), ("advection", 9, 3), ("continuity", 7, 0)])
+def test_overlapped_body_force_repeats_bitwise(model, nt, ckpt):
+    """The body force's derivative passes run on a second stream of the context while the adjoint
+    steps and segment recomputes go on in the first; adjoint states rotate through a ring of buffers and
+    recomputed segments through two, each written again only after the passes that read it are done. A
+    missing wait would let a pass read a buffer being overwritten in some calls and not in others: forty
+    gradients on a grid where the kernels do overlap are bitwise equal to the first, and with
+    checkpoints to the gradient of the stored trajectory."""
+    from paper_2510_08782_gb300 import Problem
+
+    shape, prec = (96, 96, 96), "mixed"
+    m0, m1, v = random_problem_fields(shape, 5, model=model, vel_scale_vox=3.0)
+    m0, m1, v = quantise(m0, prec), quantise(m1, prec), quantise(v, prec)
+
+    def problem(k):
+        return Problem(to_dev(m0, prec), to_dev(m1, prec), nt=nt, model=model, reg_order=1, alpha=1e-3,
+                       prec=prec, ckpt_every=k)
+
+    P = problem(ckpt)
+    vd = to_dev(v, prec)
+    g0 = empty(v.shape, prec)
+    J0 = P.gradient(vd, g0)
+    ref = host(g0)
+    g = empty(v.shape, prec)
+    for _ in range(40):
+        assert P.gradient(vd, g) == J0
+        assert np.array_equal(host(g), ref)
+    if ckpt:
+        Ps = problem(0)
+        gs = empty(v.shape, prec)
+        assert Ps.gradient(vd, gs) == J0
+        assert np.array_equal(host(gs), ref)
+
+
 def test_host_buffers_match_device_buffers():
     shape = (32, 24)
     P, O, v = _setup(shape, "fp64", "advection")
