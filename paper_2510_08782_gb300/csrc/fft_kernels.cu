@@ -1024,6 +1024,51 @@ cudaError_t launch_deriv_pair(const Grid& g, const FftTables<T>& ft, int axis, c
   return deriv_pass<T, true>(g, ft, axis, io, st);
 }
 
+// Complex transform of 16 columns per CTA along a strided 256-point axis, in registers (the four-step
+// form above, forward only): thread (p, x) loads x[x + 16 m] of column p, applies the DFT16 over m and
+// the twiddles W256^(x k2), one exchange gives it the values over q for k2 = x, and the DFT16 over q
+// leaves X[x + 16 k1] in a[k1], which it stores where it loaded. The inverse conjugates on the way in
+// and on the way out (times scale), as k_fft_cols does. Columns past nx are zero and not stored.
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_fft_cols_reg256(cx<T>* __restrict__ fh, long long S, long long outer_stride, int nx,
+                  const cx<T>* __restrict__ twg, T scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);  // W256^j, j < 256
+  cx<T>* xb = tw + 256;                             // exchange buffer, kX16P per column
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x, p = t & 15, x = t >> 4;
+  const int c0 = blockIdx.x * 16;
+  const bool v0 = c0 + p < nx;
+  const long long off = (long long)blockIdx.y * outer_stride + c0 + p + (long long)x * S;
+  const long long st16 = 16 * S;
+  cx<T> a[16];
+  {
+    const cx<T>* fp = fh + off;
+#pragma unroll
+    for (int m = 0; m < 16; ++m, fp += st16) {
+      cx<T> z = v0 ? fp[0] : mk<T>(T(0), T(0));
+      if (INV) z = cconj(z);
+      a[m] = z;
+    }
+  }
+  __syncthreads();  // twiddle table
+  dft16<T>(a);
+#pragma unroll
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+  cx<T>* xp = xb + p * kX16P;
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) xp[k2 * 17 + x] = a[k2];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = xp[x * 17 + q];  // thread holds k2 = x over q
+  dft16<T>(a);                                          // a[k1] = X[x + 16 k1]
+  if (!v0) return;
+  cx<T>* op = fh + off;
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1, op += st16) op[0] = INV ? cscale(cconj(a[k1]), scale) : a[k1];
+}
+
 template <typename T>
 static cudaError_t launch_cols(const Grid& g, const FftTables<T>& ft, int axis, cx<T>* fh, int inverse,
                                cudaStream_t st) {
@@ -1044,6 +1089,15 @@ static cudaError_t launch_cols(const Grid& g, const FftTables<T>& ft, int axis, 
     S = (long long)g.n[1] * nx;
     outer = g.n[1];
     outer_stride = nx;
+  }
+  if (L == kRegFftLen) {  // register-resident transform: 16 columns per CTA
+    auto kern = inverse ? k_fft_cols_reg256<T, true> : k_fft_cols_reg256<T, false>;
+    const size_t smr = sizeof(cx<T>) * (256 + 16 * kX16P);
+    cudaError_t e = allow_smem(kern, smr);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    kern<<<dim3((nx + 15) / 16, outer), 256, smr, st>>>(fh, S, outer_stride, nx, ft.tw[axis], T(1) / T(L));
+    return cudaGetLastError();
   }
   dim3 grid((nx + B - 1) / B, outer);
   return with_nc<T>(L, [&](auto nc) {
