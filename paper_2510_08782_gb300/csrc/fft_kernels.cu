@@ -1069,6 +1069,98 @@ k_fft_cols_reg256(cx<T>* __restrict__ fh, long long S, long long outer_stride, i
   for (int k1 = 0; k1 < 16; ++k1, op += st16) op[0] = INV ? cscale(cconj(a[k1]), scale) : a[k1];
 }
 
+// Row passes of the 3D real FFT for 256-point rows, in registers: 16 complex pencils per CTA, pencil p
+// packing rows 2p and 2p + 1 of the tile as real and imaginary parts, transformed as 16 x 16 with one
+// exchange (thread (p, x) holds the values at x + 16 m before and the bins x + 16 k1 after the
+// transform). The half spectra of the two rows, A_k = (Z_k + conj Z_{256-k}) / 2 and
+// B_k = (Z_k - conj Z_{256-k}) / (2 i), need bin 256 - k, which thread (p, (16 - x) mod 16) of the same
+// half-warp holds (in a[15 - k1], or a[(16 - k1) mod 16] when x = 0): one shuffle per bin brings it.
+template <typename T>
+__device__ __forceinline__ void reg256_forward(cx<T>* a, const cx<T>* tw, cx<T>* xp, int x) {
+  dft16<T>(a);
+#pragma unroll
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) xp[k2 * 17 + x] = a[k2];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = xp[x * 17 + q];  // thread holds k2 = x over q
+  dft16<T>(a);                                          // a[k1] = X[x + 16 k1]
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_r2c_rows_reg256(const T* __restrict__ f, cx<T>* __restrict__ fh, long long rows, const cx<T>* __restrict__ twg) {
+  constexpr int L = 256, LH = 129;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* xb = tw + L;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x, p = t >> 4, x = t & 15;
+  const long long r0 = (long long)blockIdx.x * 32 + 2 * p;
+  const bool va = r0 < rows, vb = r0 + 1 < rows;
+  cx<T> a[16];
+  {
+    const T* fa = f + r0 * L + x;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) a[m] = mk<T>(va ? fa[16 * m] : T(0), vb ? fa[L + 16 * m] : T(0));
+  }
+  __syncthreads();  // twiddle table
+  reg256_forward<T>(a, tw, xb + p * kX16P, x);
+  const int lane = t & 31, partner = (lane & 16) | ((16 - x) & 15);
+  cx<T> r[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    r[i].x = __shfl_sync(0xffffffffu, a[i].x, partner);
+    r[i].y = __shfl_sync(0xffffffffu, a[i].y, partner);
+  }
+  cx<T>* ha = fh + r0 * LH + x;
+#pragma unroll
+  for (int k1 = 0; k1 <= 8; ++k1) {
+    if (k1 == 8 && x != 0) break;  // bins x + 16 k1 <= 128
+    const cx<T> zk = a[k1];
+    const cx<T> zm = cconj(x != 0 ? r[15 - k1] : r[(16 - k1) & 15]);
+    if (va) ha[16 * k1] = cscale(cadd(zk, zm), T(0.5));
+    if (vb) ha[LH + 16 * k1] = cscale(cmul_negi(csub(zk, zm)), T(0.5));
+  }
+}
+
+// The inverse: Z_k = A_k + i B_k for k <= 128 and Z_{256-k} = conj A_k + i conj B_k, transformed
+// through conjugation; row 2p is the real part, row 2p + 1 the imaginary part (times scale).
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_c2r_rows_reg256(const cx<T>* __restrict__ fh, T* __restrict__ f, long long rows, const cx<T>* __restrict__ twg,
+                  T scale) {
+  constexpr int L = 256, LH = 129;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* xb = tw + L;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  const int t = threadIdx.x, p = t >> 4, x = t & 15;
+  const long long r0 = (long long)blockIdx.x * 32 + 2 * p;
+  const bool va = r0 < rows, vb = r0 + 1 < rows;
+  const cx<T>* ha = fh + r0 * LH;
+  const cx<T> zero = mk<T>(T(0), T(0));
+  cx<T> a[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int n = x + 16 * m;
+    const bool direct = n <= 128;
+    const int k = direct ? n : L - n;
+    const cx<T> A = va ? ha[k] : zero, Bv = vb ? ha[LH + k] : zero;
+    const cx<T> z = direct ? mk<T>(A.x - Bv.y, A.y + Bv.x) : mk<T>(A.x + Bv.y, -A.y + Bv.x);
+    a[m] = cconj(z);
+  }
+  __syncthreads();  // twiddle table
+  reg256_forward<T>(a, tw, xb + p * kX16P, x);
+  T* fa = f + r0 * L + x;
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    if (va) fa[16 * k1] = a[k1].x * scale;
+    if (vb) fa[L + 16 * k1] = -a[k1].y * scale;
+  }
+}
+
 template <typename T>
 static cudaError_t launch_cols(const Grid& g, const FftTables<T>& ft, int axis, cx<T>* fh, int inverse,
                                cudaStream_t st) {
@@ -1115,6 +1207,17 @@ template <typename T>
 cudaError_t launch_r2c(const Grid& g, const FftTables<T>& ft, const T* f, cx<T>* fh, cudaStream_t st) {
   const int L = g.n[2];
   const long long rows = (long long)g.n[0] * g.n[1];
+  if (L == kRegFftLen) {  // register-resident row pass: 32 rows per CTA
+    auto kern = k_r2c_rows_reg256<T>;
+    const size_t smr = sizeof(cx<T>) * (256 + 16 * kX16P);
+    cudaError_t e = allow_smem(kern, smr);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    kern<<<(unsigned)((rows + 31) / 32), 256, smr, st>>>(f, fh, rows, ft.tw[2]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_cols<T>(g, ft, 1, fh, 0, st)) != cudaSuccess) return e;
+    return launch_cols<T>(g, ft, 0, fh, 0, st);
+  }
   int B = batch_for<T>(L);
   if (B > (rows + 1) / 2) B = (int)((rows + 1) / 2);
   const int ld = lead_dim(L);
@@ -1143,6 +1246,14 @@ cudaError_t launch_c2r(const Grid& g, const FftTables<T>& ft, cx<T>* fh, T* f, c
   if ((e = launch_cols<T>(g, ft, 1, fh, 1, st)) != cudaSuccess) return e;
   const int L = g.n[2];
   const long long rows = (long long)g.n[0] * g.n[1];
+  if (L == kRegFftLen) {  // register-resident row pass: 32 rows per CTA
+    auto kern = k_c2r_rows_reg256<T>;
+    const size_t smr = sizeof(cx<T>) * (256 + 16 * kX16P);
+    if ((e = allow_smem(kern, smr)) != cudaSuccess) return e;
+    note_launches(1);
+    kern<<<(unsigned)((rows + 31) / 32), 256, smr, st>>>(fh, f, rows, ft.tw[2], T(1) / T(L));
+    return cudaGetLastError();
+  }
   int B = deriv_batch<T>(L);  // the staged half-spectrum block uses the multiplier/accumulator area
   if (B > (rows + 1) / 2) B = (int)((rows + 1) / 2);
   const int ld = lead_dim(L);
