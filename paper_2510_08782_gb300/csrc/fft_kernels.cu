@@ -417,6 +417,13 @@ k_deriv_cols(DerivIO<T> io, int Lr, long long S, long long outer_stride, int nx,
 // cover consecutive columns). PAIR: pencil p is f + i f2 of one row/column (two time steps of the body
 // force); otherwise pencil p packs rows/columns 2p and 2p + 1 of f.
 constexpr int kX16P = 16 * 17 + 1;  // pencil stride of the exchange buffer
+// Twiddles of the 256-point four-step transform as a 16 x 16 table, entry b * 16 + a = W256^(a b):
+// thread x reads entry k * 16 + x for W256^(x k). The lanes of a half-warp share k and differ in x
+// (pencils along rows) or read one entry (pencils along columns), so every read is free of bank
+// conflicts (a table of W256^j indexed by x k would put lanes k entries apart).
+template <typename T> __device__ __forceinline__ void load_tw256(cx<T>* tw, const cx<T>* __restrict__ twg) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) tw[i] = twg[(i >> 4) * (i & 15)];
+}
 
 template <typename T> __device__ __forceinline__ void idft16(cx<T>* a) {
 #pragma unroll
@@ -428,14 +435,14 @@ template <typename T> __device__ __forceinline__ void idft16(cx<T>* a) {
 
 // The derivative of 16 complex pencils held in registers (see above): on entry thread (p, x) holds
 // x[x + 16 m] of its pencil in a[m]; on return a[n2] holds 256 times the derivative at x + 16 n2.
-// tw: W256^j in shared memory; xp: this pencil's exchange area. Contains the CTA barriers of the two
+// tw: the 16 x 16 twiddle table in shared memory (load_tw256); xp: this pencil's exchange area. Contains the CTA barriers of the two
 // exchanges, so every thread of the CTA calls it.
 template <typename T>
 __device__ __forceinline__ void reg256_deriv(cx<T>* a, const cx<T>* tw, cx<T>* xp, int x) {
   // load phase: DFT16 over m, twiddles W256^(q k2), exchange
   dft16<T>(a);
 #pragma unroll
-  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[k2 * 16 + x]);
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) xp[k2 * 17 + x] = a[k2];
   __syncthreads();
@@ -452,7 +459,7 @@ __device__ __forceinline__ void reg256_deriv(cx<T>* a, const cx<T>* tw, cx<T>* x
   // inverse: DFT16 over k1 with conjugate weights, twiddles W256^(-n1 k2), exchange, DFT16 over k2
   idft16<T>(a);  // a[n1]
 #pragma unroll
-  for (int n1 = 1; n1 < 16; ++n1) a[n1] = cmul(a[n1], cconj(tw[n1 * x]));
+  for (int n1 = 1; n1 < 16; ++n1) a[n1] = cmul(a[n1], cconj(tw[n1 * 16 + x]));
   __syncthreads();  // every thread has read its exchange entries
 #pragma unroll
   for (int n1 = 0; n1 < 16; ++n1) xp[n1 * 17 + x] = a[n1];
@@ -467,9 +474,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_deriv_reg256(DerivIO<T> io, long long npen, long long S, long long outer_stride, const cx<T>* __restrict__ twg) {
   constexpr int L = 256;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);  // W256^j, j < 256
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);  // W256^(a b) at b * 16 + a (load_tw256)
   cx<T>* xb = tw + L;                               // exchange buffer
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  load_tw256<T>(tw, twg);
   const int t = threadIdx.x;
   const int p = ROWS ? (t >> 4) : (t & 15);  // complex pencil of the tile
   const int x = ROWS ? (t & 15) : (t >> 4);  // q, then k2, then n1
@@ -564,7 +571,7 @@ __device__ __forceinline__ void xchg_split(float2* a, float* xr, int x) {
 __device__ __forceinline__ void reg256_deriv_split(float2* a, const float2* tw, float* xr, int x) {
   dft16<float>(a);
 #pragma unroll
-  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[k2 * 16 + x]);
   xchg_split(a, xr, x);  // thread holds k2 = x over q
   dft16<float>(a);       // a[k1] = X[x + 16 k1]
 #pragma unroll
@@ -575,7 +582,7 @@ __device__ __forceinline__ void reg256_deriv_split(float2* a, const float2* tw, 
   }
   idft16<float>(a);  // a[n1]
 #pragma unroll
-  for (int n1 = 1; n1 < 16; ++n1) a[n1] = cmul(a[n1], cconj(tw[n1 * x]));
+  for (int n1 = 1; n1 < 16; ++n1) a[n1] = cmul(a[n1], cconj(tw[n1 * 16 + x]));
   __syncthreads();  // every thread has read the first exchange
   xchg_split(a, xr, x);  // thread holds n1 = x over k2
   idft16<float>(a);      // a[n2]: 256 times the derivative at x + 16 n2
@@ -646,7 +653,7 @@ k_deriv_pair256s(DerivIO<float> io, long long npen, long long S, long long outer
     }
   }
   cpa_commit();
-  for (int i = t; i < L; i += blockDim.x) tw[i] = twg[i];
+  load_tw256<float>(tw, twg);
   const bool v0 = p < valid;
   const long long off = base + (ROWS ? (long long)p * L + x : p + (long long)x * S);
   const long long st16 = ROWS ? 16 : 16 * S;
@@ -1034,9 +1041,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_fft_cols_reg256(cx<T>* __restrict__ fh, long long S, long long outer_stride, int nx,
                   const cx<T>* __restrict__ twg, T scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);  // W256^j, j < 256
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);  // W256^(a b) at b * 16 + a (load_tw256)
   cx<T>* xb = tw + 256;                             // exchange buffer, kX16P per column
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) tw[i] = twg[i];
+  load_tw256<T>(tw, twg);
   const int t = threadIdx.x, p = t & 15, x = t >> 4;
   const int c0 = blockIdx.x * 16;
   const bool v0 = c0 + p < nx;
@@ -1055,7 +1062,7 @@ k_fft_cols_reg256(cx<T>* __restrict__ fh, long long S, long long outer_stride, i
   __syncthreads();  // twiddle table
   dft16<T>(a);
 #pragma unroll
-  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[k2 * 16 + x]);
   cx<T>* xp = xb + p * kX16P;
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) xp[k2 * 17 + x] = a[k2];
@@ -1079,7 +1086,7 @@ template <typename T>
 __device__ __forceinline__ void reg256_forward(cx<T>* a, const cx<T>* tw, cx<T>* xp, int x) {
   dft16<T>(a);
 #pragma unroll
-  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[x * k2]);
+  for (int k2 = 1; k2 < 16; ++k2) a[k2] = cmul(a[k2], tw[k2 * 16 + x]);
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) xp[k2 * 17 + x] = a[k2];
   __syncthreads();
@@ -1095,7 +1102,7 @@ k_r2c_rows_reg256(const T* __restrict__ f, cx<T>* __restrict__ fh, long long row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* xb = tw + L;
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  load_tw256<T>(tw, twg);
   const int t = threadIdx.x, p = t >> 4, x = t & 15;
   const long long r0 = (long long)blockIdx.x * 32 + 2 * p;
   const bool va = r0 < rows, vb = r0 + 1 < rows;
@@ -1135,7 +1142,7 @@ k_c2r_rows_reg256(const cx<T>* __restrict__ fh, T* __restrict__ f, long long row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* xb = tw + L;
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+  load_tw256<T>(tw, twg);
   const int t = threadIdx.x, p = t >> 4, x = t & 15;
   const long long r0 = (long long)blockIdx.x * 32 + 2 * p;
   const bool va = r0 < rows, vb = r0 + 1 < rows;
