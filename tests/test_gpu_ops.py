@@ -123,13 +123,21 @@ AXES_256 = [(256, 6, 10), (4, 256, 18), (6, 10, 256), (5, 9, 256)]
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", AXES_256)
 def test_register_transform_on_256_axes(shape, prec):
-    """The register-resident derivative passes of 256-point axes: along the contiguous axis (rows; 45
-    rows leave the last packed pencil without a partner) and along strided axes (columns; partial last
-    tiles), for one field (ga_op_deriv) and for two time steps at once (the body force)."""
+    """The register-resident passes of 256-point axes: along the contiguous axis (rows; 45 rows leave
+    the last packed pencil without a partner) and along strided axes (columns; partial last tiles of
+    the 129 half-spectrum columns), for the 3D real transform and its inverse, for one field
+    (ga_op_deriv) and for two time steps at once (the body force)."""
     import paper_2510_08782_gb300 as ga
 
     P, m0, _, v = _problem(shape, prec, model="advection", nt=4)
     f = quantise(random_fourier_field(shape, 1, 6, np.random.default_rng(4))[0], prec)
+    fh = empty(shape[:-1] + (shape[-1] // 2 + 1, 2), prec)
+    ga.ga_op_fft_r2c(P.ctx, P.dtype, to_dev(f, prec), fh)
+    fref = np.fft.rfftn(f)
+    assert rel_l2(host(fh), np.stack([fref.real, fref.imag], axis=-1)) < TOL[prec]
+    back = empty(shape, prec)
+    ga.ga_op_fft_c2r(P.ctx, P.dtype, fh, back)
+    assert rel_l2(host(back), f) < TOL[prec]
     ref = osp.grad(f)
     for a in range(3):
         out = empty(shape, prec)
