@@ -309,16 +309,25 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
   const bool active = gx < n2 && gy < n1;
   const int nz = min(ZB, n0 - bi.bz * ZB);
   const long long idx0 = ((long long)(bi.bz * ZB) * n1 + gy) * n2 + gx;
+  // This column's fields from per-thread base pointers with 32-bit offsets v * pl (an axis has at most
+  // 1024 points, so a field's offsets fit in 32 bits).
+  const int pl = n1 * n2;
+  const float* dz0 = disp + idx0;
+  const float* dy0 = dz0 + nv;
+  const float* dx0 = dy0 + nv;
+  const float* mu0 = NF == 2 ? mu + idx0 : nullptr;
+  float* out0 = out + idx0;
+  float2* q0 = (NF == 2 && qout) ? qout + idx0 : nullptr;
   // Displacements (and mu at the voxel) of one pair ahead are kept in registers: the first pair's are
   // requested while the tile is still being copied, each later pair's while the previous one is
   // interpolated.
   float za = 0.f, zb = 0.f, ya = 0.f, yb = 0.f, xa = 0.f, xb = 0.f, ma = 0.f, mb = 0.f;
   auto fetch = [&](int v) {
-    const long long ia = idx0 + v * plane, ib = ia + plane;
-    za = disp[ia], zb = disp[ib];
-    ya = disp[nv + ia], yb = disp[nv + ib];
-    xa = disp[2 * nv + ia], xb = disp[2 * nv + ib];
-    if (NF == 2) ma = mu[ia], mb = mu[ib];
+    const int oa = v * pl, ob = oa + pl;
+    za = dz0[oa], zb = dz0[ob];
+    ya = dy0[oa], yb = dy0[ob];
+    xa = dx0[oa], xb = dx0[ob];
+    if (NF == 2) ma = mu0[oa], mb = mu0[ob];
   };
   if (NF == 1 && active && nz >= 2) fetch(0);
   if (NF == 2 && active && nz >= 2) {
@@ -366,7 +375,7 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
   int v = 0;
 #pragma unroll 1
   for (; v + 1 < nz; v += 2) {
-    const long long ia = idx0 + v * plane, ib = ia + plane;
+    const int oa = v * pl, ob = oa + pl;
     const float cza = za, czb = zb, cya = ya, cyb = yb, cxa = xa, cxb = xb, cma = ma, cmb = mb;
     if (v + 3 < nz) fetch(v + 2);
     const float fza = floorf(cza), fya = floorf(cya), fxa = floorf(cxa);
@@ -384,24 +393,25 @@ __device__ __forceinline__ void sl_tile_body(const float* __restrict__ f, const 
         lagrange4v(vsplat<float2>(cxa - fxa), wx);
         const float2 A = interp64<TXP, float2>(wz, wy, wx, [&](int o) { return sp[ba + o]; });
         const float ya = step_value<MODE>(A.x, A.y, cma, ht);
-        out[ia] = ya;
-        if (qout) qout[ia] = make_float2(ya, ya * cma);
+        out0[oa] = ya;
+        if (q0) q0[oa] = make_float2(ya, ya * cma);
         lagrange4v(vsplat<float2>(czb - fzb), wz);
         lagrange4v(vsplat<float2>(cyb - fyb), wy);
         lagrange4v(vsplat<float2>(cxb - fxb), wx);
         const float2 B = interp64<TXP, float2>(wz, wy, wx, [&](int o) { return sp[bb + o]; });
         const float yb = step_value<MODE>(B.x, B.y, cmb, ht);
-        out[ib] = yb;
-        if (qout) qout[ib] = make_float2(yb, yb * cmb);
+        out0[ob] = yb;
+        if (q0) q0[ob] = make_float2(yb, yb * cmb);
       } else {  // one field: the pair of voxels as one packed pair
         lagrange4v(make_float2(cza - fza, czb - fzb), wz);
         lagrange4v(make_float2(cya - fya, cyb - fyb), wy);
         lagrange4v(make_float2(cxa - fxa, cxb - fxb), wx);
         const float2 P = interp64<TXA, float2>(wz, wy, wx, [&](int o) { return make_float2(sf[ba + o], sf[bb + o]); });
-        out[ia] = step_value<MODE>(P.x, 0.f, cma, ht);
-        out[ib] = step_value<MODE>(P.y, 0.f, cmb, ht);
+        out0[oa] = step_value<MODE>(P.x, 0.f, cma, ht);
+        out0[ob] = step_value<MODE>(P.y, 0.f, cmb, ht);
       }
     } else {
+      const long long ia = idx0 + oa, ib = idx0 + ob;
       sl_single<MODE>(f, mu, out, qout, sf, col, ia, bi.bz * ZB + v, v, gy, gx, cza, cya, cxa, n0, n1, n2, ht);
       sl_single<MODE>(f, mu, out, qout, sf, col, ib, bi.bz * ZB + v + 1, v + 1, gy, gx, czb, cyb, cxb, n0, n1, n2, ht);
     }
