@@ -47,10 +47,10 @@ REF_SAMPLE_N = 48  # oracle sample grid of each step of the reference arm
 PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ, PROF_DERIV_PAIR = 0, 1, 2, 3, 4
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sl_tile2<1> launch from an ncu
-# capture of this benchmark at 192^3 (chained state steps at brick depth 12: 171.7 MB read + 57.9 MB
-# written, mean of 3 launches), scaled to n^3 by the voxel count. Valid for the kernel as captured, at
-# that brick depth; None while the kernel has changed since the last capture.
-SL_FWD_TRAFFIC_192 = 229.6e6
+# capture of this benchmark at 192^3 (`--sl-depth 12,8`: chained state steps at brick depth 12,
+# 171.7 MB read + 55.6 MB written, mean of 3 launches), scaled to n^3 by the voxel count. Valid for the
+# kernel as captured, at that brick depth; None while the kernel has changed since the last capture.
+SL_FWD_TRAFFIC_192 = 227.3e6
 SL_FWD_TRAFFIC_DEPTH = 12
 
 
@@ -540,6 +540,10 @@ def main():
                          "mixed path against it")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batch of 32 uneven advection problems (both batched forms)")
+    ap.add_argument("--sl-depth", default=None,
+                    help="STATE,ADJOINT: fix the transport steps' brick depths (4, 8 or 12) instead of the "
+                         "setup autotuner's choice, e.g. for a profiler run, whose timing the autotuner "
+                         "would otherwise measure")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -568,6 +572,8 @@ def main():
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
     m0, m1 = dev(w["m0"]), dev(w["m1"])
     P = ga.Problem(m0, m1, prec="mixed", **SETTINGS)
+    if args.sl_depth:
+        ga.ga_op_set_sl_depth(P.ctx, *(int(x) for x in args.sl_depth.split(",")))
     v = torch.zeros((3,) + shape, dtype=torch.float32, device="cuda")
 
     def barrier():
