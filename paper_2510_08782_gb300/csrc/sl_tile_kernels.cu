@@ -144,7 +144,7 @@ __device__ __forceinline__ void stage_async(float* dst, const float* __restrict_
       gz = gz < 0 ? gz + n0 : (gz >= n0 ? gz - n0 : gz);
       int gx = gx0 + 4 * cx;
       gx = gx < 0 ? gx + n2 : (gx >= n2 ? gx - n2 : gx);
-      cp_async16(dst + row * TXA + 4 * cx, src + ((size_t)gz * n1 + gy) * n2 + gx);
+      cp_async16(dst + row * TXA + 4 * cx, src + ((gz * n1 + gy) * n2 + gx));  // < 2^30: axes <= 1024
     }
   } else {
     for (int e = threadIdx.x; e < TILEA; e += blockDim.x) {
@@ -177,8 +177,8 @@ __device__ __forceinline__ void stage_pairs_async(float2* dst, const float2* __r
       gz = gz < 0 ? gz + n0 : (gz >= n0 ? gz - n0 : gz);
       int gx = gx0 + 2 * cx;
       gx = gx < 0 ? gx + n2 : (gx >= n2 ? gx - n2 : gx);
-      cp_async16(reinterpret_cast<float*>(dst + row * TXP + 2 * cx), reinterpret_cast<const float*>(
-                                                                          src + ((size_t)gz * n1 + gy) * n2 + gx));
+      cp_async16(reinterpret_cast<float*>(dst + row * TXP + 2 * cx),
+                 reinterpret_cast<const float*>(src + ((gz * n1 + gy) * n2 + gx)));  // < 2^30: axes <= 1024
     }
   } else {
     for (int e = threadIdx.x; e < TXA * TY * TZ; e += blockDim.x) {
