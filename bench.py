@@ -48,9 +48,9 @@ PROF_SL_FWD, PROF_DERIV, PROF_FFT, PROF_SL_ADJ, PROF_DERIV_PAIR = 0, 1, 2, 3, 4
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sl_tile2<1> launch from an ncu
 # capture of this benchmark at 192^3 (`--sl-depth 12,8`: chained state steps at brick depth 12,
-# 171.7 MB read + 55.6 MB written, mean of 3 launches), scaled to n^3 by the voxel count. Valid for the
+# 171.7 MB read + 55.7 MB written, mean of 3 launches), scaled to n^3 by the voxel count. Valid for the
 # kernel as captured, at that brick depth; None while the kernel has changed since the last capture.
-SL_FWD_TRAFFIC_192 = 227.3e6
+SL_FWD_TRAFFIC_192 = 227.4e6
 SL_FWD_TRAFFIC_DEPTH = 12
 
 
